@@ -1,0 +1,315 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: numerical
+quadrature of the Hankel transform (Eq. (11)), closed forms of the
+band-limited Gaussian, Poisson summation, DFT inversion at lattice points,
+exact translation identities, brute force on tiny inputs, and the far-field
+error bound of the scaled Lemma (Eq. (33)).
+"""
+import itertools
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+import oracle as O
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+# ---------------------------------------------------------------- T-FT ----
+@pytest.mark.parametrize("d", [1, 2, 3, 5])
+def test_gaussian_ft_matches_hankel_quadrature(d):
+    """Eq. (11) by quadrature vs the oracle's closed-form Gaussian transform.
+
+    The oracle's closed-form coefficients are C = (2pi)^-d Phi_hat with
+    Phi_hat(xi) = (pi/eps^2)^{d/2} exp(-|xi|^2/(4 eps^2)) (Eq. (5) convention);
+    the table of transforms (Sec. 3) prints the same function times (2pi)^{-d/2}."""
+    eps, M, L = 1.5, 8, 3.0
+    wc = O.coeffs_closed_gaussian(eps, d, M, L)
+    xi, w = O.freq_grid(M, L)
+    # one-dimensional cut through the grid along dimension 0, others at xi=0
+    mid = M // 2
+    idx = [mid + (M + 1) * 0] * 1
+    for kk in range(M + 1):
+        m = kk + sum(mid * (M + 1) ** t for t in range(1, d))
+        wprod = w[kk] * w[mid] ** (d - 1)
+        phi_hat = wc[m] / wprod * (2 * np.pi) ** d
+        r = abs(xi[kk])
+        nu = (d - 2) / 2.0
+        if r == 0.0:
+            # limit r -> 0 of Eq. (11): surface area form
+            ref = (2 * np.pi) ** (d / 2) * integrate.quad(
+                lambda t: np.exp(-(eps * t) ** 2) * t ** (d - 1) / (2 ** nu * special.gamma(nu + 1)),
+                0, np.inf)[0]
+        else:
+            ref = (2 * np.pi) ** (d / 2) * r ** (-nu) * integrate.quad(
+                lambda t: np.exp(-(eps * t) ** 2) * t ** (d / 2) * special.jv(nu, r * t),
+                0, 12.0 / eps, limit=400)[0]
+        table = np.exp(-(r / eps) ** 2 / 4) / np.sqrt(2) ** d / eps ** d * (2 * np.pi) ** (d / 2)
+        assert abs(phi_hat - ref) <= 1e-10 * max(1.0, abs(ref))
+        assert abs(phi_hat - table) <= 1e-12 * max(1.0, abs(table))
+    assert idx  # silence linters
+
+
+@pytest.mark.parametrize("d", [1, 3, 5])
+def test_imq_table_row_matches_hankel(d):
+    """The table's IMQ row sqrt(2/pi) K_nu(|xi|)/|xi|^nu, nu=(d-1)/2, times (2pi)^{d/2},
+    is Eq. (11) of 1/sqrt(1+t^2).  Pins the (2pi)^{-d/2} normalisation reading
+    that the coefficient formula corrects for."""
+    nu = (d - 1) / 2.0
+    for r in (0.7, 1.9, 4.0):
+        table = (2 * np.pi) ** (d / 2) * np.sqrt(2 / np.pi) * special.kv(nu, r) / r ** nu
+        # Eq. (11) with J_{(d-2)/2}; oscillatory tail handled by quad's Fourier weight
+        # via the closed forms of J for half-integer order (d odd).
+        if d == 1:
+            val = 2 * integrate.quad(lambda t: 1 / np.sqrt(1 + t * t), 0, np.inf, weight="cos", wvar=r)[0]
+        elif d == 3:
+            val = 4 * np.pi / r * integrate.quad(lambda t: t / np.sqrt(1 + t * t), 0, np.inf,
+                                                 weight="sin", wvar=r)[0]
+        else:  # d == 5: J_{3/2}(z) = sqrt(2/(pi z)) (sin z / z - cos z)
+            c = (2 * np.pi) ** 2.5 * r ** -1.5 * np.sqrt(2 / (np.pi * r))
+            s1 = integrate.quad(lambda t: t / np.sqrt(1 + t * t) / r, 0, np.inf, weight="sin", wvar=r)[0]
+            s2 = integrate.quad(lambda t: t * t / np.sqrt(1 + t * t) - t, 0, np.inf, weight="cos", wvar=r)[0]
+            s2 += -1.0 / r ** 2  # int_0^inf t cos(rt) dt in the Abel sense
+            val = c * (s1 - s2)
+        assert abs(val - table) <= 2e-6 * abs(table)
+
+
+# ------------------------------------------------------------- T-BL ------
+def _bl_gauss_1d(t, eps, sigma):
+    """(1/2pi) int_{-sigma}^{sigma} phi_hat(xi) e^{i xi t} dxi for phi = exp(-(eps t)^2),
+    closed form exp(-(eps t)^2) Re erf(sigma/(2 eps) + i eps t), evaluated through
+    the Faddeeva function to avoid overflow."""
+    a = sigma / (2 * eps)
+    b = eps * np.asarray(t, dtype=np.float64)
+    val = np.exp(-b * b) - np.exp(-a * a) * np.exp(-2j * a * b) * special.wofz(-b + 1j * a)
+    return val.real
+
+
+def test_bandlimited_gaussian_closed_form_and_bound():
+    """Sec. 3.2's band-limited integral, closed form vs quadrature, and the
+    band-limit error |Phi_sigma - Phi| <= erfc(sigma/(2 eps))."""
+    eps, sigma = 4.0, 20.0
+    ts = np.linspace(-1.2, 1.2, 41)
+    for t in ts[::5]:
+        q = integrate.quad(lambda x: np.sqrt(np.pi) / eps * np.exp(-x * x / (4 * eps * eps)) * np.cos(x * t),
+                           -sigma, sigma, limit=200)[0] / (2 * np.pi)
+        assert abs(_bl_gauss_1d(t, eps, sigma) - q) < 1e-13
+    err = np.max(np.abs(_bl_gauss_1d(ts, eps, sigma) - np.exp(-(eps * ts) ** 2)))
+    # the bound is attained at t = 0, where Phi_sigma(0) = erf(sigma/(2 eps))
+    assert err <= special.erfc(sigma / (2 * eps)) * (1 + 1e-12)
+    assert err > 0.999 * special.erfc(sigma / (2 * eps))
+
+
+# -------------------------------------------------------------- T-Q ------
+@pytest.mark.parametrize("d", [1, 2])
+def test_poisson_closed_form_coefficients(d):
+    """With closed-form C, K(r) = prod_t sum_n Phi_sigma(r_t + nL) (Poisson summation),
+    where Phi_sigma is the band-limited Gaussian.  The band edge is kept large
+    (exp(-sigma^2/(4eps^2)) ~ 1e-4) so the half weights at +-sigma matter."""
+    eps, M, L = 4.0, 16, 2.5
+    sigma = np.pi * M / L
+    wc = O.coeffs_closed_gaussian(eps, d, M, L)
+    rng = np.random.default_rng(5)
+    r = rng.uniform(-1.0, 1.0, (12, d))
+    K = O.kernel_K(wc, d, M, L, r)
+    # the image sum converges like 1/n (sinc tail of Phi_sigma): symmetric partial
+    # sums S_N, S_2N and one Richardson step 2 S_2N - S_N remove the 1/N term
+    def image_sum(x, nmax):
+        n = np.arange(-nmax, nmax + 1)
+        return np.sum(_bl_gauss_1d(x + n * L, eps, sigma))
+    ref = np.ones(len(r))
+    for t in range(d):
+        ref *= np.array([2 * image_sum(x, 200000) - image_sum(x, 100000) for x in r[:, t]])
+    assert np.max(np.abs(K - ref)) < 1e-12
+    assert np.max(np.abs(K - np.exp(-eps ** 2 * np.sum(r * r, axis=1)))) > 1e-5  # band edge visible
+
+
+# ------------------------------------------------------------ T-SAMP -----
+@pytest.mark.parametrize("kernel,eps,d,M,L,alpha", [(O.IMQ, 2.0, 2, 16, 4.0, 4.5),
+                                                    (O.IMQ, 2.0, 3, 12, 4.0, 4.5),
+                                                    (O.GAUSSIAN, 3.0, 3, 10, 3.0, 0.0)])
+def test_sampled_coefficients_interpolate_lattice(kernel, eps, d, M, L, alpha):
+    """DFT inversion: with sampled C, K(qh) equals the periodised, windowed sample f(q)
+    exactly, and f(q) is Phi(qh) inside the window's flat part."""
+    wc = O.coeffs_sampled(kernel, eps, d, M, L, alpha, 1.0)
+    f = O.lattice_samples(kernel, eps, d, M, L, alpha, 1.0)
+    h = L / M
+    qs = np.array(list(itertools.product(range(-M // 2, M // 2), repeat=d)))
+    rng = np.random.default_rng(2)
+    pick = qs[rng.choice(len(qs), size=min(200, len(qs)), replace=False)]
+    K = O.kernel_K(wc, d, M, L, pick * h)
+    fv = f[tuple((pick + M // 2).T)]
+    assert np.max(np.abs(K - fv)) < 1e-13 * max(1.0, np.max(np.abs(fv)))
+    inner = np.max(np.abs(pick * h), axis=1) <= 1.0
+    phi_v = O.phi(kernel, eps, np.linalg.norm(pick[inner] * h, axis=1))
+    assert np.max(np.abs(fv[inner] - phi_v)) < 2e-9
+
+
+def test_sampled_matches_closed_form_gaussian():
+    """For the Gaussian with negligible images, the sampled coefficients are the
+    closed-form Fourier transform up to aliasing (Eq. (M2Loperator) vs Eq. (29))."""
+    eps, d, M, L = 3.0, 2, 32, 3.0
+    a = O.coeffs_sampled(O.GAUSSIAN, eps, d, M, L, 0.0, 1.0)
+    b = O.coeffs_closed_gaussian(eps, d, M, L)
+    assert np.max(np.abs(a - b)) < 1e-10 * np.max(np.abs(b))
+
+
+# ------------------------------------------------------------ T-TREE -----
+def _tree_case(d, N, D, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.random((N, d))
+    # points on faces, edges and the far corner exercise floor + clamp
+    X[0] = 1.0
+    X[1] = 0.5
+    X[2, 0] = 0.0
+    X[3] = 0.25
+    return X
+
+
+def test_morton_keys_by_hand():
+    """Keys from the definition, worked by hand (d=2, D=2, dimension 0 in bit 0):
+    (0.3, 0.8) -> k=(1,3) -> bits (k0b0,k1b0,k0b1,k1b1)=(1,1,0,1) -> 11;
+    (1.0, 0.0) -> k=(3,0) (clamped) -> (1,0,1,0) -> 5;  (0.5, 0.5) -> k=(2,2) -> 12."""
+    X = np.array([[0.3, 0.8], [1.0, 0.0], [0.5, 0.5]])
+    T = O.tree(X, np.zeros(2), 1.0, 2)
+    assert sorted(T["keys"].tolist()) == [5, 11, 12]
+    assert T["perm"].tolist() == [1, 0, 2]
+
+
+@pytest.mark.parametrize("d,N,D", [(2, 300, 3), (3, 400, 3), (2, 200, 4)])
+def test_lists_cover_every_pair_once(d, N, D):
+    """Every ordered pair (i, j) is either near (leaf Chebyshev distance <= 1) or in
+    exactly one interaction list IL_l, l = 2..D; lists match brute-force definitions."""
+    X = _tree_case(d, N, D, seed=d * 10 + D)
+    T = O.tree(X, np.zeros(d), 1.0, D)
+    # brute-force box coordinates of every point at every level, by repeated halving
+    kD = np.empty((N, d), dtype=np.int64)
+    for i in range(N):
+        for t in range(d):
+            kD[i, t] = min(max(int(np.floor(X[i, t] * 2 ** D)), 0), 2 ** D - 1)
+    leaf_of_orig = np.searchsorted(T["leaf_key"], O.morton_encode(kD, d, D))
+    count = np.zeros((N, N), dtype=np.int64)
+    near_sets = [set(T["near_idx"][T["near_off"][a]:T["near_off"][a + 1]].tolist())
+                 for a in range(len(T["leaf_key"]))]
+    for i in range(N):
+        for j in range(N):
+            cheb = np.max(np.abs(kD[i] - kD[j]))
+            is_near = leaf_of_orig[j] in near_sets[leaf_of_orig[i]]
+            assert is_near == (cheb <= 1)
+            count[i, j] += is_near
+    for l in range(2, D + 1):
+        lv = T["levels"][l]
+        kl = kD >> (D - l)
+        box = np.searchsorted(lv["key"], O.morton_encode(kl, d, l))
+        ils = [set(lv["il_idx"][lv["il_off"][a]:lv["il_off"][a + 1]].tolist())
+               for a in range(len(lv["key"]))]
+        for i in range(N):
+            for j in range(N):
+                inil = box[j] in ils[box[i]]
+                parent_near = np.max(np.abs((kl[i] >> 1) - (kl[j] >> 1))) <= 1
+                far = np.max(np.abs(kl[i] - kl[j])) >= 2
+                assert inil == (parent_near and far)
+                count[i, j] += inil
+    assert np.all(count == 1)
+    # sizes: |N_a| <= 3^d, |IL| <= 6^d - 3^d
+    assert np.max(np.diff(T["near_off"])) <= 3 ** d
+    for l in range(2, D + 1):
+        assert np.max(np.diff(T["levels"][l]["il_off"])) <= 6 ** d - 3 ** d
+
+
+# ------------------------------------------------------------ T-CONS -----
+def test_translation_consistency():
+    """M2M(P2M(children)) = P2M at the parent and L2P(L2L(L_p)) = L2P of L_p at the
+    parent: exact on one shared grid (Eqs. (43), (48) with P = I)."""
+    d, D, M, L = 2, 3, 12, 3.0
+    rng = np.random.default_rng(7)
+    X = rng.random((300, d))
+    lam = rng.standard_normal(300)
+    T = O.tree(X, np.zeros(d), 1.0, D)
+    ls = lam[T["perm"]]
+    V3 = O.p2m(T, ls, M, L)
+    V2 = O.m2m(T, V3, 3, M, L)
+    # P2M straight at level 2: points grouped by their level-2 box
+    lv2 = T["levels"][2]
+    leaf_par = T["levels"][3]["parent"]
+    off2 = np.searchsorted(T["leaf_off"][:-1], T["leaf_off"][:-1])  # identity, for clarity
+    pt_off2 = np.array([T["leaf_off"][np.searchsorted(leaf_par, b)] for b in range(len(lv2["key"]))]
+                       + [T["N"]])
+    T2 = dict(T, leaf_key=lv2["key"], leaf_off=pt_off2, D=2)
+    V2_direct = O.p2m(T2, ls, M, L)
+    assert off2 is not None
+    assert rel(V2, V2_direct) < 1e-13
+    # L2P(L2L(Lp)) vs L2P of Lp at the parent level
+    Lp = rng.standard_normal(V2.shape) + 1j * rng.standard_normal(V2.shape)
+    Lc = np.zeros_like(V3)
+    O.l2l(T, Lp, Lc, 3, M, L)
+    u_child = np.zeros(T["N"])
+    O.l2p(T, Lc, M, L, u_child)
+    u_par = np.zeros(T["N"])
+    O.l2p(T2, Lp, M, L, u_par)
+    assert rel(u_child, u_par) < 1e-13
+
+
+# ----------------------------------------------------------- T-BRUTE -----
+@pytest.mark.parametrize("d,N,D,kernel,eps,M,L,alpha", [
+    (2, 400, 3, O.GAUSSIAN, 4.0, 24, 2.5, 0.0),
+    (2, 300, 4, O.IMQ, 2.0, 16, 4.0, 4.5),
+    (3, 250, 3, O.IMQ, 2.0, 10, 4.0, 4.5),
+    (3, 200, 2, O.GAUSSIAN, 3.0, 12, 3.0, 0.0),
+])
+def test_fmm_equals_bruteforce(d, N, D, kernel, eps, M, L, alpha):
+    """The multilevel FMM (P2M, M2M, M2L over IL_l, L2L, L2P) equals the direct sum of
+    Phi over near pairs and K over all other pairs, computed pair by pair."""
+    rng = np.random.default_rng(N + d)
+    X = rng.random((N, d))
+    lam = rng.standard_normal(N)
+    T = O.tree(X, np.zeros(d), 1.0, D)
+    wc = O.coeffs_sampled(kernel, eps, d, M, L, alpha, 1.0)
+    u = O.fmm(T, lam, kernel, eps, wc, M, L)
+    ub = O.fmm_brute(T, lam, kernel, eps, wc, M, L)
+    assert rel(u, ub) < 1e-13
+    ut = O.fmm_at_targets(T, lam, kernel, eps, wc, M, L, np.arange(0, N, 5))
+    assert rel(ut, u[::5]) < 1e-13
+
+
+# ------------------------------------------------------------- T-ERR -----
+def test_fmm_error_within_lemma_bound_config1():
+    """d=2, N=4096, Gaussian eps=4, depth 3: |u_fmm - u_direct|_i is bounded by
+    max_far |K - Phi| * sum_j |lambda_j| (scaled Lemma, Eq. (33)); the actual
+    relative L2 error is small."""
+    from workloads import config1
+    X, lam, p = config1()
+    T = O.tree(X, np.zeros(2), 1.0, p["depth"])
+    wc = O.coeffs_sampled(O.GAUSSIAN, p["eps"], 2, p["M"], p["L"], p["alpha"], 1.0)
+    u = O.fmm(T, lam, O.GAUSSIAN, p["eps"], wc, p["M"], p["L"])
+    ud = O.direct(X, lam, O.GAUSSIAN, p["eps"])
+    rng = np.random.default_rng(11)
+    r = rng.uniform(-1, 1, (4000, 2))
+    r = r[np.max(np.abs(r), axis=1) >= 1.0 / 8]
+    kerr = np.max(np.abs(O.kernel_K(wc, 2, p["M"], p["L"], r) - O.phi(O.GAUSSIAN, p["eps"],
+                                                                       np.linalg.norm(r, axis=1))))
+    bound = kerr * np.sum(np.abs(lam))
+    assert np.max(np.abs(u - ud)) <= bound
+    assert rel(u, ud) < 1e-10
+
+
+# ------------------------------------------------------- direct sum ------
+def test_direct_sum_small_cases():
+    """Eq. (1) on two points, and the Gershgorin bound gamma_max <= N max|Phi|."""
+    X = np.array([[0.0, 0.0], [0.3, 0.4]])
+    lam = np.array([2.0, -1.0])
+    u = O.direct(X, lam, O.GAUSSIAN, 2.0)
+    g = np.exp(-(2.0 * 0.5) ** 2)
+    assert np.allclose(u, [2.0 - g, 2.0 * g - 1.0], rtol=0, atol=1e-15)
+    u = O.direct(X, lam, O.IMQ, 2.0)
+    q = 1 / np.sqrt(1 + 1.0)
+    assert np.allclose(u, [2.0 - q, 2.0 * q - 1.0], rtol=0, atol=1e-15)
+    rng = np.random.default_rng(3)
+    Y = rng.random((60, 3))
+    A = np.stack([O.direct(Y, e, O.IMQ, 2.0) for e in np.eye(60)], axis=1)
+    assert np.allclose(A, A.T, atol=1e-15)
+    assert np.max(np.linalg.eigvalsh(A)) <= 60 * 1.0
