@@ -1,0 +1,223 @@
+/*
+ * rbf.h -- C ABI of the GB300 (sm_103a) band-limited FMM for radial basis
+ * function interpolation, after Zhao & Stoll, "A Fast Multipole Method based
+ * on Band-limited Approximations for Radial Basis Functions" (arXiv 1606.07652).
+ *
+ * The library computes u = A lambda with A_ij = Phi(x_i - x_j) (Eq. (1)) by the
+ * paper's FMM: a near field summed point to point over neighbour leaves and a
+ * far field carried by exponential (band-limited Fourier quadrature)
+ * expansions, Eqs. (35)-(38), (43)-(48), (54).  It also solves A lambda = u
+ * with GMRES driven by that product (Sec. 1).
+ *
+ * Conventions for every entry point:
+ *  - Pointers are DEVICE pointers unless the name ends in _host.  The caller
+ *    owns every pointer it passes; the library never frees them.
+ *  - The library owns rbf_tree and everything hanging off it (sorted points,
+ *    lists, coefficient tables, expansion workspace); rbf_tree_free releases it.
+ *  - Every call returns an int: RBF_OK (0) or a negative RBF_E* code; no C++
+ *    exception crosses the ABI.  rbf_last_error() gives a message for the last
+ *    failure on the calling thread.
+ *  - Work is enqueued on `stream` (a cudaStream_t, or NULL for the legacy
+ *    default stream).  Calls that return results in host memory synchronise
+ *    that stream before they return; the others are asynchronous.
+ *  - Vectors lambda and u are in the caller's original point order; the
+ *    Morton permutation is internal.  Several right-hand sides are stored
+ *    column-major with a leading dimension (ld >= N).
+ *  - A tree is not thread-safe: calls on one tree must not overlap in time.
+ */
+#ifndef RBF_H
+#define RBF_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RBF_API __attribute__((visibility("default")))
+#else
+#define RBF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RBF_OK 0
+#define RBF_EINVAL (-1)   /* bad argument (null pointer, size, parameter range) */
+#define RBF_ENOMEM (-2)   /* device allocation failed */
+#define RBF_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define RBF_ENOCONV (-4)  /* iterative solve stopped before reaching rtol */
+#define RBF_ETIMEOUT (-5) /* a bounded device-side wait ran out */
+#define RBF_ENOTSUP (-6)  /* combination not supported by this build */
+
+#define RBF_MAX_DIM 6
+#define RBF_MAX_DEPTH 10
+
+/* Radial kernels of the table "Global functions" (Sec. 2.2) in shape-parameter
+ * form: Gaussian Phi(r) = exp(-(eps r)^2); inverse multiquadric
+ * Phi(r) = 1/sqrt(1 + (eps r)^2).  Both have Phi(0) = 1. */
+typedef enum { RBF_GAUSSIAN = 0, RBF_IMQ = 1 } rbf_kernel;
+
+/* Arithmetic of the matrix-vector product.  Inputs and outputs of
+ * rbf_fmm_matvec are FP64 in both cases. */
+typedef enum { RBF_FP64 = 0, RBF_FP32 = 1 } rbf_precision;
+
+/* Parameters of the band-limited expansion (Sec. 3.2, "Low-rank representation").
+ *  M            quadrature nodes per dimension (even, 2..64).  The nodes are
+ *               xi_k = k * 2pi/L, k = -M/2..M/2, with half weight at +-M/2,
+ *               so the band limit is sigma = pi M / L.
+ *  period_L     period of the sampled kernel; must exceed twice the root side.
+ *  window_alpha steepness of the erfc taper applied to slowly decaying kernels
+ *               before periodisation (0 = no taper).  The taper is flat on
+ *               |t| <= side and falls to ~0 at |t| = L - side.
+ *  csample      1: C(xi) from samples of Phi on the lattice h Z^d, h = L/M
+ *               (Eq. (M2Loperator), the paper's kernel-independent route);
+ *               0: closed-form Gaussian transform (validation, Gaussian only). */
+typedef struct {
+    int M;
+    double period_L;
+    double window_alpha;
+    int csample;
+} rbf_fmm_params;
+
+typedef struct rbf_tree rbf_tree;
+
+/* Summary of a built tree (host struct). */
+typedef struct {
+    int64_t N;
+    int d;
+    int depth;                 /* D: leaves are the level-D boxes */
+    double lo[RBF_MAX_DIM];    /* root cube [lo, lo + side]^d */
+    double side;
+    int64_t n_leaf;            /* non-empty leaves */
+    int64_t n_near;            /* entries of all near lists */
+    int64_t max_leaf_points;   /* largest leaf */
+    int64_t n_box[RBF_MAX_DEPTH + 1]; /* non-empty boxes per level */
+} rbf_tree_info;
+
+/* Build the Morton tree of the centres (Sec. 1, "hierarchical tree
+ * partitioning"; groups G_b and neighbour lists N_a of Eq. (38)).
+ *  X        device, [N][d] row-major FP64, caller's order.
+ *  N        number of centres, 1 <= N < 2^31.
+ *  d        dimension, 1..RBF_MAX_DIM.
+ *  lo_host  host array of d doubles, the root cube's lower corner, or NULL to
+ *           use the bounding box of X (then `side` is ignored and set to the
+ *           largest extent).
+ *  side     root cube edge (> 0) when lo_host is given.
+ *  depth    D, 0..RBF_MAX_DEPTH with d*D <= 63; depth < 0 picks
+ *           round(log_{2^d}(N/32)) clamped to [2, RBF_MAX_DEPTH].
+ *  out      receives the new tree (NULL on failure).
+ * Box coordinates are k_t = min(max(floor(((x_t-lo_t)/side)*2^D), 0), 2^D-1)
+ * in FP64; Morton keys put dimension 0 in bit 0; the sort is stable by
+ * (key, original index).  Synchronises `stream`. */
+RBF_API int rbf_tree_build(const double *X, int64_t N, int d, const double *lo_host, double side, int depth,
+                   void *stream, rbf_tree **out);
+
+/* Fill *info_host.  No device work. */
+RBF_API int rbf_tree_get_info(const rbf_tree *t, rbf_tree_info *info_host);
+
+/* Copy the tree to host arrays for bit-exact checks; any pointer may be NULL.
+ *  perm[N]            sorted position -> original index
+ *  keys[N]            Morton keys of the sorted points
+ *  leaf_key[n_leaf]   Morton keys of the non-empty leaves, ascending
+ *  leaf_off[n_leaf+1] first sorted point of each leaf
+ *  near_off[n_leaf+1], near_idx[n_near]  CSR near lists N_a (compact leaf ids,
+ *                     ascending; leaves at Chebyshev index distance <= 1,
+ *                     self included).  Synchronises `stream`. */
+RBF_API int rbf_tree_export(const rbf_tree *t, int64_t *perm, uint64_t *keys, uint64_t *leaf_key,
+                    int64_t *leaf_off, int64_t *near_off, int64_t *near_idx, void *stream);
+
+/* Interaction lists IL_l of the MLFMM coupling step (Sec. 4.1, Eq. (45)) for one
+ * level 2 <= l <= D: level-l boxes whose parents are within Chebyshev distance
+ * 1 of the parent of a and which are at distance >= 2 from a.  Built on the
+ * device on first request.  box_key[n_box[l]] (ascending Morton keys of the
+ * non-empty level-l boxes), il_off[n_box[l]+1], il_idx[*n_il_host] (compact
+ * level-l ids, ascending).  Pass il_idx = NULL to query *n_il_host first.
+ * Synchronises `stream`. */
+RBF_API int rbf_tree_export_level(rbf_tree *t, int level, uint64_t *box_key, int64_t *il_off,
+                          int64_t *il_idx, int64_t *n_il_host, void *stream);
+
+/* u = A lambda by the band-limited FMM (Eqs. (38), (54)):
+ *   u_i = sum_{j in near leaves} lambda_j Phi(x_i - x_j)
+ *       + sum_{other j} lambda_j K(x_i - x_j),
+ *   K(r) = sum_xi omega(xi) C(xi) e^{i xi . r}   (Eq. (35)).
+ * Passes: near field, P2M at the leaves (Eq. (P2M)), M2M upsweep (Eq. (43),
+ * one shared grid), coupling (Eq. (45)), downsweep to the leaves (Eq. (48)),
+ * L2P (Eq. (46)).
+ *  lambda   device FP64, N x nrhs column-major, leading dimension ld_lambda.
+ *  u        device FP64, N x nrhs column-major, leading dimension ld_u; written.
+ *  prec     RBF_FP64 or RBF_FP32 arithmetic for every pass.
+ *  params   expansion parameters (see rbf_fmm_params); NULL = defaults
+ *           (M=32, L=4 side, alpha=4.5 for IMQ, 0 for Gaussian, csample=1).
+ * Coefficient tables and expansion workspace are built on first use and kept
+ * in the tree until the parameters change.  Asynchronous. */
+RBF_API int rbf_fmm_matvec(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_params *params,
+                   rbf_precision prec, const double *lambda, int64_t ld_lambda, double *u,
+                   int64_t ld_u, int nrhs, void *stream);
+
+/* Same product with host buffers: copies lambda_host to the device, runs
+ * rbf_fmm_matvec, copies u back.  Synchronises `stream`. */
+RBF_API int rbf_fmm_matvec_host(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_params *params,
+                        rbf_precision prec, const double *lambda_host, double *u_host, int nrhs,
+                        void *stream);
+
+/* Plain O(N^2) sum of Eq. (1) in FP64 at selected targets (error checks):
+ *  X [N][d] row-major, lambda [N], targets [nt] (indices into X), u [nt]. */
+RBF_API int rbf_direct_sum(const double *X, int64_t N, int d, rbf_kernel kernel, double eps,
+                   const double *lambda, const int64_t *targets, int64_t nt, double *u, void *stream);
+
+/* Solver options for rbf_interp_solve (Sec. 1: GMRES with the FMM product).
+ *  restart_m   Krylov dimension per restart (1..200).
+ *  max_iters   total inner iterations over all restarts and refinements.
+ *  max_refine  outer FP64 refinement steps (>= 1).
+ *  rtol        target ||u - A lambda||_2 / ||u||_2, measured with the FP64 FMM.
+ *  inner_prec  arithmetic of the matvec inside GMRES (RBF_FP64 or RBF_FP32).
+ *  precond     0: none (the diagonal of A is Phi(0) = 1, so the diagonal
+ *              preconditioner is the identity); 1: learned sparse approximate
+ *              inverse (set with rbf_precond_set). */
+typedef struct {
+    int restart_m;
+    int max_iters;
+    int max_refine;
+    double rtol;
+    rbf_precision inner_prec;
+    int precond;
+} rbf_solve_opts;
+
+/* Per-solve report (host struct). */
+typedef struct {
+    int iters;            /* inner GMRES iterations, all restarts */
+    int refinements;      /* outer refinement steps taken */
+    int used_fallback;    /* 1 when the learned preconditioner was dropped */
+    double rel_resid;     /* final ||u - A64 lambda|| / ||u|| */
+    double seconds;       /* wall time of the solve */
+    int matvecs_inner;    /* products in inner arithmetic */
+    int matvecs_fp64;     /* FP64 products for true residuals */
+} rbf_solve_report;
+
+/* Solve A lambda = u (one right-hand side at a time, nrhs columns) with
+ * restarted, right-preconditioned GMRES (two-pass classical Gram-Schmidt,
+ * Givens rotations; FP64 basis) inside an FP64 iterative-refinement loop:
+ * r = u - A64 lambda, GMRES on A delta = r with the inner-precision matvec,
+ * lambda += delta, until ||r||/||u|| <= rtol.  lambda holds the initial guess
+ * on entry (zero it for a cold start) and the solution on return.
+ * u, lambda: device FP64 N x nrhs, leading dimension N.  rep_host may be NULL.
+ * Returns RBF_ENOCONV (lambda still holds the best iterate) when the budget
+ * runs out.  Synchronises `stream`. */
+RBF_API int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_params *params,
+                     const double *u, double *lambda, int nrhs, const rbf_solve_opts *opts,
+                     rbf_solve_report *rep_host, void *stream);
+
+/* Release a tree and everything it owns.  NULL is accepted. */
+RBF_API void rbf_tree_free(rbf_tree *t);
+
+/* Message for a status code, and the detail of the last failure on this thread. */
+RBF_API const char *rbf_strerror(int code);
+RBF_API const char *rbf_last_error(void);
+
+/* Library version, "major.minor.patch". */
+RBF_API const char *rbf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBF_H */

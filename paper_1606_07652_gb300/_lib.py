@@ -1,0 +1,259 @@
+"""ctypes binding of librbf.so: argument marshalling only.
+
+Every function mirrors an entry point of include/rbf.h.  Device vectors are
+torch CUDA tensors (their data_ptr is passed); host vectors are numpy arrays.
+Work is enqueued on torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+GAUSSIAN = 0
+IMQ = 1
+FP64 = 0
+FP32 = 1
+MAX_DIM = 6
+MAX_DEPTH = 10
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "librbf.so")
+_lib = None
+
+_c_int, _c_i64, _c_dbl, _c_vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+
+class FmmParams(ctypes.Structure):
+    _fields_ = [("M", _c_int), ("period_L", _c_dbl), ("window_alpha", _c_dbl), ("csample", _c_int)]
+
+
+class TreeInfo(ctypes.Structure):
+    _fields_ = [("N", _c_i64), ("d", _c_int), ("depth", _c_int), ("lo", _c_dbl * MAX_DIM),
+                ("side", _c_dbl), ("n_leaf", _c_i64), ("n_near", _c_i64),
+                ("max_leaf_points", _c_i64), ("n_box", _c_i64 * (MAX_DEPTH + 1))]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("restart_m", _c_int), ("max_iters", _c_int), ("max_refine", _c_int),
+                ("rtol", _c_dbl), ("inner_prec", _c_int), ("precond", _c_int)]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [("iters", _c_int), ("refinements", _c_int), ("used_fallback", _c_int),
+                ("rel_resid", _c_dbl), ("seconds", _c_dbl), ("matvecs_inner", _c_int),
+                ("matvecs_fp64", _c_int)]
+
+
+class RbfError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = load().rbf_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {load().rbf_strerror(code).decode()} ({code}): {msg}")
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load librbf.so (built by __graft_entry__.build() or paper_1606_07652_gb300/build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"librbf.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P = ctypes.POINTER
+    lib.rbf_tree_build.argtypes = [_c_vp, _c_i64, _c_int, _c_vp, _c_dbl, _c_int, _c_vp,
+                                   P(_c_vp)]
+    lib.rbf_tree_get_info.argtypes = [_c_vp, P(TreeInfo)]
+    lib.rbf_tree_export.argtypes = [_c_vp] + [_c_vp] * 6 + [_c_vp]
+    lib.rbf_tree_export_level.argtypes = [_c_vp, _c_int, _c_vp, _c_vp, _c_vp, P(_c_i64), _c_vp]
+    lib.rbf_fmm_matvec.argtypes = [_c_vp, _c_int, _c_dbl, P(FmmParams), _c_int, _c_vp, _c_i64,
+                                   _c_vp, _c_i64, _c_int, _c_vp]
+    lib.rbf_fmm_matvec_host.argtypes = [_c_vp, _c_int, _c_dbl, P(FmmParams), _c_int, _c_vp,
+                                        _c_vp, _c_int, _c_vp]
+    lib.rbf_direct_sum.argtypes = [_c_vp, _c_i64, _c_int, _c_int, _c_dbl, _c_vp, _c_vp, _c_i64,
+                                   _c_vp, _c_vp]
+    lib.rbf_interp_solve.argtypes = [_c_vp, _c_int, _c_dbl, P(FmmParams), _c_vp, _c_vp, _c_int,
+                                     P(SolveOpts), P(SolveReport), _c_vp]
+    lib.rbf_tree_free.argtypes = [_c_vp]
+    lib.rbf_tree_free.restype = None
+    lib.rbf_strerror.argtypes = [_c_int]
+    lib.rbf_strerror.restype = ctypes.c_char_p
+    lib.rbf_last_error.restype = ctypes.c_char_p
+    lib.rbf_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(code, where):
+    if code != 0:
+        raise RbfError(code, where)
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype_name, where):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{where}: expected a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"{where}: expected {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{where}: tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def version() -> str:
+    return load().rbf_version().decode()
+
+
+def _params(M=None, period_L=None, window_alpha=None, csample=1, kernel=GAUSSIAN, side=1.0):
+    if M is None and period_L is None and window_alpha is None:
+        return None
+    p = FmmParams()
+    p.M = 32 if M is None else int(M)
+    p.period_L = 4.0 * side if period_L is None else float(period_L)
+    if window_alpha is None:
+        window_alpha = 4.5 if kernel == IMQ else 0.0
+    p.window_alpha = float(window_alpha)
+    p.csample = int(csample)
+    return p
+
+
+class Tree:
+    """Owner of an rbf_tree handle (freed with rbf_tree_free)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = TreeInfo()
+        _check(load().rbf_tree_get_info(self._h, ctypes.byref(inf)), "rbf_tree_get_info")
+        d = inf.d
+        return {"N": inf.N, "d": d, "depth": inf.depth, "lo": list(inf.lo)[:d], "side": inf.side,
+                "n_leaf": inf.n_leaf, "n_near": inf.n_near, "max_leaf_points": inf.max_leaf_points,
+                "n_box": list(inf.n_box)[:inf.depth + 1]}
+
+    def export(self) -> dict:
+        inf = self.info()
+        N, nl, nn = inf["N"], inf["n_leaf"], inf["n_near"]
+        out = {"perm": np.empty(N, np.int64), "keys": np.empty(N, np.uint64),
+               "leaf_key": np.empty(nl, np.uint64), "leaf_off": np.empty(nl + 1, np.int64),
+               "near_off": np.empty(nl + 1, np.int64), "near_idx": np.empty(max(nn, 1), np.int64)}
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+        _check(load().rbf_tree_export(self._h, ptr(out["perm"]), ptr(out["keys"]),
+                                      ptr(out["leaf_key"]), ptr(out["leaf_off"]),
+                                      ptr(out["near_off"]), ptr(out["near_idx"]), _stream()),
+               "rbf_tree_export")
+        out["near_idx"] = out["near_idx"][:nn]
+        return out
+
+    def export_level(self, level: int) -> dict:
+        inf = self.info()
+        n_il = _c_i64(0)
+        lib = load()
+        _check(lib.rbf_tree_export_level(self._h, level, None, None, None, ctypes.byref(n_il),
+                                         _stream()), "rbf_tree_export_level")
+        nb = inf["n_box"][level]
+        key = np.empty(nb, np.uint64)
+        off = np.empty(nb + 1, np.int64)
+        idx = np.empty(max(n_il.value, 1), np.int64)
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+        _check(lib.rbf_tree_export_level(self._h, level, ptr(key), ptr(off), ptr(idx),
+                                         ctypes.byref(n_il), _stream()), "rbf_tree_export_level")
+        return {"key": key, "il_off": off, "il_idx": idx[:n_il.value]}
+
+    def free(self):
+        if self._h:
+            load().rbf_tree_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def tree_build(X, lo=None, side=1.0, depth=-1) -> Tree:
+    """rbf_tree_build: X is a contiguous float64 CUDA tensor of shape (N, d)."""
+    N, d = X.shape
+    px = _dev(X, "float64", "tree_build X")
+    lo_arr = None
+    if lo is not None:
+        lo_arr = (ctypes.c_double * d)(*[float(v) for v in np.asarray(lo).reshape(d)])
+    h = ctypes.c_void_p()
+    _check(load().rbf_tree_build(px, N, d, lo_arr, float(side), int(depth), _stream(),
+                                 ctypes.byref(h)), "rbf_tree_build")
+    return Tree(h)
+
+
+def fmm_matvec(tree: Tree, kernel: int, eps: float, lam, u, prec=FP64, M=None, period_L=None,
+               window_alpha=None, csample=1):
+    """rbf_fmm_matvec: lam, u are float64 CUDA tensors (N,) or (nrhs, N) (rows = columns of
+    the column-major N x nrhs block)."""
+    nrhs = 1 if lam.dim() == 1 else lam.shape[0]
+    N = lam.shape[-1]
+    p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"])
+    _check(load().rbf_fmm_matvec(tree.handle, kernel, float(eps),
+                                 ctypes.byref(p) if p is not None else None, prec,
+                                 _dev(lam, "float64", "lam"), N, _dev(u, "float64", "u"), N, nrhs,
+                                 _stream()), "rbf_fmm_matvec")
+    return u
+
+
+def fmm_matvec_host(tree: Tree, kernel: int, eps: float, lam_host, prec=FP64, M=None,
+                    period_L=None, window_alpha=None, csample=1):
+    """rbf_fmm_matvec_host: numpy float64 in, numpy float64 out (host <-> device inside)."""
+    lam_host = np.ascontiguousarray(lam_host, dtype=np.float64)
+    nrhs = 1 if lam_host.ndim == 1 else lam_host.shape[0]
+    u = np.empty_like(lam_host)
+    p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"])
+    _check(load().rbf_fmm_matvec_host(tree.handle, kernel, float(eps),
+                                      ctypes.byref(p) if p is not None else None, prec,
+                                      ctypes.c_void_p(lam_host.ctypes.data),
+                                      ctypes.c_void_p(u.ctypes.data), nrhs, _stream()),
+           "rbf_fmm_matvec_host")
+    return u
+
+
+def direct_sum(X, kernel: int, eps: float, lam, targets, u):
+    """rbf_direct_sum: X (N, d) float64, lam (N,), targets (nt,) int64, u (nt,) CUDA tensors."""
+    N, d = X.shape
+    _check(load().rbf_direct_sum(_dev(X, "float64", "X"), N, d, kernel, float(eps),
+                                 _dev(lam, "float64", "lam"), _dev(targets, "int64", "targets"),
+                                 targets.shape[0], _dev(u, "float64", "u"), _stream()),
+           "rbf_direct_sum")
+    return u
+
+
+def interp_solve(tree: Tree, kernel: int, eps: float, u, lam, restart_m=50, max_iters=2000,
+                 max_refine=10, rtol=1e-8, inner_prec=FP32, precond=0, M=None, period_L=None,
+                 window_alpha=None, csample=1):
+    """rbf_interp_solve: u, lam float64 CUDA tensors (N,) or (nrhs, N); lam holds the guess."""
+    nrhs = 1 if u.dim() == 1 else u.shape[0]
+    o = SolveOpts(restart_m, max_iters, max_refine, rtol, inner_prec, precond)
+    rep = SolveReport()
+    p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"])
+    code = load().rbf_interp_solve(tree.handle, kernel, float(eps),
+                                   ctypes.byref(p) if p is not None else None,
+                                   _dev(u, "float64", "u"), _dev(lam, "float64", "lam"), nrhs,
+                                   ctypes.byref(o), ctypes.byref(rep), _stream())
+    report = {"status": code, "iters": rep.iters, "refinements": rep.refinements,
+              "used_fallback": rep.used_fallback, "rel_resid": rep.rel_resid,
+              "seconds": rep.seconds, "matvecs_inner": rep.matvecs_inner,
+              "matvecs_fp64": rep.matvecs_fp64}
+    if code not in (0, -4):
+        raise RbfError(code, "rbf_interp_solve")
+    return report

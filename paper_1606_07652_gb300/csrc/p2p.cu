@@ -1,0 +1,260 @@
+// p2p.cu -- near field of Eq. (38) (the sparse part A^diag + A^near-diag of
+// Eq. (54)) and the plain O(N^2) sum of Eq. (1).
+//
+// Near field: one CTA per target leaf a.  The points of the neighbour leaves
+// N_a are staged from HBM into shared memory in chunks (coordinates and lambda
+// as one 16-byte record per point in FP32, two in FP64); each warp takes a
+// quarter of the staged sources, lane = target, so every shared-memory read is
+// a broadcast.  The four partial sums of a target are added in a fixed order.
+#include <algorithm>
+
+#include "rbf_internal.cuh"
+
+namespace {
+
+constexpr int P2P_THREADS = 128;
+constexpr int P2P_WARPS = P2P_THREADS / 32;
+constexpr int P2P_TGROUPS = 8;                 // target groups of 32 per pass
+constexpr int P2P_TBLOCK = 32 * P2P_TGROUPS;   // targets per pass
+constexpr int P2P_STAGE_BYTES = 16384;         // shared memory for staged sources
+
+template <typename R>
+struct Src4;
+template <>
+struct Src4<float> {
+    using type = float4;
+};
+template <>
+struct Src4<double> {
+    using type = double4_32a;
+};
+
+// Phi in the product's arithmetic: exp(-(eps r)^2) or 1/sqrt(1 + (eps r)^2).
+__device__ __forceinline__ float phi_r2(int kernel, float e2, float r2)
+{
+    // Gaussian through exp2: e2 already holds eps^2 * log2(e)
+    return kernel == RBF_GAUSSIAN ? exp2f(-e2 * r2) : rsqrtf(fmaf(e2, r2, 1.0f));
+}
+__device__ __forceinline__ double phi_r2(int kernel, double e2, double r2)
+{
+    return kernel == RBF_GAUSSIAN ? exp(-e2 * r2) : rsqrt(fma(e2, r2, 1.0));
+}
+
+template <typename R, int DIM>
+__global__ void __launch_bounds__(P2P_THREADS) k_p2p(int kernel, R e2, int64_t N, const R *xs,
+                                                     const R *lam, const int32_t *leaf_off,
+                                                     const int32_t *near_off,
+                                                     const int32_t *near_idx, R *u)
+{
+    using S4 = typename Src4<R>::type;
+    // per source: (x0, x1, x2, lambda) for DIM <= 3; DIM > 3 uses two records
+    constexpr int REC = DIM <= 3 ? 1 : 2;
+    constexpr int P2P_SCHUNK = P2P_STAGE_BYTES / (int)(sizeof(S4) * REC);
+    __shared__ S4 src[P2P_SCHUNK * REC];
+    __shared__ int32_t rstart[729], rlen[729], rpre[730];
+    __shared__ R red[P2P_WARPS][P2P_TBLOCK];
+    const int a = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int e0 = near_off[a], ne = near_off[a + 1] - e0;
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int e = 0; e < ne; ++e) {
+            int b = near_idx[e0 + e];
+            rstart[e] = leaf_off[b];
+            rlen[e] = leaf_off[b + 1] - leaf_off[b];
+            rpre[e] = run;
+            run += rlen[e];
+        }
+        rpre[ne] = run;
+    }
+    __syncthreads();
+    const int nsrc = rpre[ne];
+    const int t0 = leaf_off[a], nt = leaf_off[a + 1] - t0;
+    for (int tb = 0; tb < nt; tb += P2P_TBLOCK) {
+        R xt[P2P_TGROUPS][DIM];
+        R acc[P2P_TGROUPS];
+#pragma unroll
+        for (int g = 0; g < P2P_TGROUPS; ++g) {
+            int i = tb + g * 32 + lane;
+            acc[g] = (R)0;
+#pragma unroll
+            for (int t = 0; t < DIM; ++t) xt[g][t] = i < nt ? xs[(int64_t)t * N + t0 + i] : (R)0;
+        }
+        for (int s0 = 0; s0 < nsrc; s0 += P2P_SCHUNK) {
+            const int cnt = min(P2P_SCHUNK, nsrc - s0);
+            __syncthreads();
+            for (int v = threadIdx.x; v < cnt; v += P2P_THREADS) {
+                // virtual source index -> neighbour range (<= 3^d ranges)
+                int vv = s0 + v, lo = 0, hi = ne - 1;
+                while (lo < hi) {  // last range with rpre[e] <= vv
+                    int mid = (lo + hi + 1) >> 1;
+                    if (rpre[mid] <= vv) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int e = lo;
+                int64_t j = rstart[e] + (vv - rpre[e]);
+                R c[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
+#pragma unroll
+                for (int t = 0; t < DIM; ++t) c[t] = xs[(int64_t)t * N + j];
+                if (REC == 1) {
+                    S4 r;
+                    r.x = c[0];
+                    r.y = c[1];
+                    r.z = c[2];
+                    r.w = lam[j];
+                    src[v] = r;
+                } else {
+                    S4 r0, r1;
+                    r0.x = c[0];
+                    r0.y = c[1];
+                    r0.z = c[2];
+                    r0.w = lam[j];
+                    r1.x = c[3];
+                    r1.y = c[4];
+                    r1.z = c[5];
+                    r1.w = (R)0;
+                    src[2 * v] = r0;
+                    src[2 * v + 1] = r1;
+                }
+            }
+            __syncthreads();
+            const int ngrp = min(P2P_TGROUPS, (nt - tb + 31) / 32);
+            for (int j = warp; j < cnt; j += P2P_WARPS) {
+                S4 r0 = src[REC * j];
+                S4 r1;
+                if (REC == 2) r1 = src[2 * j + 1];
+#pragma unroll
+                for (int g = 0; g < P2P_TGROUPS; ++g) {
+                    if (g < ngrp) {
+                        R d0 = xt[g][0] - r0.x;
+                        R r2 = d0 * d0;
+                        if (DIM > 1) {
+                            R d1 = xt[g][DIM > 1 ? 1 : 0] - r0.y;
+                            r2 = fma(d1, d1, r2);
+                        }
+                        if (DIM > 2) {
+                            R d2 = xt[g][DIM > 2 ? 2 : 0] - r0.z;
+                            r2 = fma(d2, d2, r2);
+                        }
+                        if (DIM > 3) {
+                            R d3 = xt[g][DIM > 3 ? 3 : 0] - r1.x;
+                            r2 = fma(d3, d3, r2);
+                        }
+                        if (DIM > 4) {
+                            R d4 = xt[g][DIM > 4 ? 4 : 0] - r1.y;
+                            r2 = fma(d4, d4, r2);
+                        }
+                        if (DIM > 5) {
+                            R d5 = xt[g][DIM > 5 ? 5 : 0] - r1.z;
+                            r2 = fma(d5, d5, r2);
+                        }
+                        acc[g] = fma(r0.w, phi_r2(kernel, e2, r2), acc[g]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int g = 0; g < P2P_TGROUPS; ++g) red[warp][g * 32 + lane] = acc[g];
+        __syncthreads();
+        for (int i = threadIdx.x; i < min(P2P_TBLOCK, nt - tb); i += P2P_THREADS) {
+            R s = red[0][i];
+#pragma unroll
+            for (int w = 1; w < P2P_WARPS; ++w) s += red[w][i];
+            u[t0 + tb + i] = s;
+        }
+    }
+}
+
+template <typename R>
+int launch_p2p(int d, int kernel, R e2, const rbf_tree *t, const R *xs, const R *lam, R *u,
+               cudaStream_t s)
+{
+    const int nleaf = t->nleaf();
+    switch (d) {
+#define RBF_P2P_CASE(DD)                                                                          \
+    case DD:                                                                                      \
+        k_p2p<R, DD><<<nleaf, P2P_THREADS, 0, s>>>(kernel, e2, t->N, xs, lam, t->leaf_off,         \
+                                                   t->near_off, t->near_idx, u);                   \
+        break;
+        RBF_P2P_CASE(1)
+        RBF_P2P_CASE(2)
+        RBF_P2P_CASE(3)
+        RBF_P2P_CASE(4)
+        RBF_P2P_CASE(5)
+        RBF_P2P_CASE(6)
+#undef RBF_P2P_CASE
+        default:
+            rbf_set_error("p2p: unsupported dimension %d", d);
+            return RBF_EINVAL;
+    }
+    RBF_LAUNCH_CHECK();
+    return RBF_OK;
+}
+
+// ------------------------------------------------------- direct sum -------
+constexpr int DS_THREADS = 256;
+constexpr int DS_TILE = 256;
+
+__global__ void __launch_bounds__(DS_THREADS) k_direct(const double *X, int64_t N, int d, int kernel,
+                                                       double eps, const double *lam,
+                                                       const int64_t *targets, int64_t nt,
+                                                       double *u)
+{
+    __shared__ double sx[DS_TILE * RBF_MAX_DIM];
+    __shared__ double sl[DS_TILE];
+    const int64_t q = (int64_t)blockIdx.x * DS_THREADS + threadIdx.x;
+    double xt[RBF_MAX_DIM];
+    const bool active = q < nt;
+    const int64_t ti = active ? targets[q] : 0;
+    for (int t = 0; t < d; ++t) xt[t] = active ? X[ti * d + t] : 0.0;
+    const double e2 = eps * eps;
+    double acc = 0.0;
+    for (int64_t j0 = 0; j0 < N; j0 += DS_TILE) {
+        const int cnt = (int)min((int64_t)DS_TILE, N - j0);
+        __syncthreads();
+        for (int v = threadIdx.x; v < cnt * d; v += DS_THREADS) sx[v] = X[j0 * d + v];
+        for (int v = threadIdx.x; v < cnt; v += DS_THREADS) sl[v] = lam[j0 + v];
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+            double r2 = 0.0;
+            for (int t = 0; t < d; ++t) {
+                double df = xt[t] - sx[j * d + t];
+                r2 += df * df;
+            }
+            acc += sl[j] * (kernel == RBF_GAUSSIAN ? exp(-e2 * r2) : 1.0 / sqrt(1.0 + e2 * r2));
+        }
+    }
+    if (active) u[q] = acc;
+}
+
+}  // namespace
+
+template <typename R>
+int rbf_run_p2p(const rbf_tree *t, int kernel, double eps, const R *lam_s, R *u, cudaStream_t s)
+{
+    const R *xs = (const R *)(sizeof(R) == 8 ? (const void *)t->xs64 : (const void *)t->xs32);
+    // the FP32 Gaussian goes through exp2, so fold log2(e) into eps^2
+    double e2 = eps * eps;
+    if (sizeof(R) == 4 && kernel == RBF_GAUSSIAN) e2 *= 1.4426950408889634;
+    return launch_p2p<R>(t->d, kernel, (R)e2, t, xs, lam_s, u, s);
+}
+
+template int rbf_run_p2p<float>(const rbf_tree *, int, double, const float *, float *, cudaStream_t);
+template int rbf_run_p2p<double>(const rbf_tree *, int, double, const double *, double *,
+                                 cudaStream_t);
+
+extern "C" int rbf_direct_sum(const double *X, int64_t N, int d, rbf_kernel kernel, double eps,
+                              const double *lambda, const int64_t *targets, int64_t nt, double *u,
+                              void *stream)
+{
+    RBF_REQUIRE(X && lambda && targets && u, "rbf_direct_sum: NULL pointer");
+    RBF_REQUIRE(N >= 1 && d >= 1 && d <= RBF_MAX_DIM && nt >= 0, "rbf_direct_sum: bad sizes");
+    RBF_REQUIRE(kernel == RBF_GAUSSIAN || kernel == RBF_IMQ, "rbf_direct_sum: unknown kernel");
+    if (nt == 0) return RBF_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_direct<<<ceil_div(nt, DS_THREADS), DS_THREADS, 0, s>>>(X, N, d, kernel, eps, lambda, targets,
+                                                             nt, u);
+    RBF_LAUNCH_CHECK();
+    return RBF_OK;
+}

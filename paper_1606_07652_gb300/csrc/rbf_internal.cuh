@@ -1,0 +1,181 @@
+// rbf_internal.cuh -- internal types and helpers of the sm_103a library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/rbf.h"
+
+// ---------------------------------------------------------------- errors --
+void rbf_set_error(const char *fmt, ...);
+
+#define RBF_CUDA_TRY(expr)                                                                  \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess) {                                                            \
+            rbf_set_error("%s:%d: %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(_e)); \
+            return RBF_ECUDA;                                                               \
+        }                                                                                   \
+    } while (0)
+
+#define RBF_LAUNCH_CHECK() RBF_CUDA_TRY(cudaGetLastError())
+
+#define RBF_TRY(expr)               \
+    do {                            \
+        int _s = (expr);            \
+        if (_s != RBF_OK) return _s; \
+    } while (0)
+
+#define RBF_REQUIRE(cond, ...)            \
+    do {                                  \
+        if (!(cond)) {                    \
+            rbf_set_error(__VA_ARGS__);   \
+            return RBF_EINVAL;            \
+        }                                 \
+    } while (0)
+
+int rbf_malloc(void **p, size_t bytes);
+template <typename T>
+inline int rbf_alloc(T **p, size_t count)
+{
+    return rbf_malloc(reinterpret_cast<void **>(p), count * sizeof(T));
+}
+void rbf_free(void *p);
+
+// --------------------------------------------------------------- complex --
+template <typename R>
+struct cplx_t;
+template <>
+struct cplx_t<float> {
+    using type = float2;
+};
+template <>
+struct cplx_t<double> {
+    using type = double2;
+};
+template <typename R>
+using cplx = typename cplx_t<R>::type;
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b)
+{
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+// acc += a * b
+template <typename C>
+__device__ __forceinline__ void cmac(C &acc, C a, C b)
+{
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cmac(float2 &acc, float2 a, float2 b)
+{
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+template <typename C>
+__device__ __forceinline__ C cconj(C a)
+{
+    a.y = -a.y;
+    return a;
+}
+
+__device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
+
+// ----------------------------------------------------------------- tree ---
+struct rbf_level {
+    int32_t nbox = 0;
+    uint64_t *key = nullptr;       // [nbox] ascending Morton keys at this level
+    int32_t *parent = nullptr;     // [nbox] compact id at level-1 (levels >= 1)
+    int32_t *child_off = nullptr;  // [nbox+1] children range at level+1 (levels < D)
+    int32_t *il_off = nullptr;     // [nbox+1] interaction lists (levels >= 2, lazy)
+    int32_t *il_idx = nullptr;
+    int64_t n_il = -1;
+};
+
+struct rbf_plan;  // expansion tables + workspace, one per precision
+
+struct rbf_tree {
+    int64_t N = 0;
+    int d = 0, D = 0;
+    double lo[RBF_MAX_DIM] = {0};
+    double side = 1.0;
+    // sorted points
+    uint64_t *keys = nullptr;   // [N]
+    int32_t *perm = nullptr;    // [N] sorted -> original
+    double *xs64 = nullptr;     // SoA [d][N]
+    float *xs32 = nullptr;      // SoA [d][N]
+    // leaves = level-D boxes
+    int32_t *leaf_off = nullptr;    // [nleaf+1]
+    int32_t *near_off = nullptr;    // [nleaf+1]
+    int32_t *near_idx = nullptr;    // [n_near]
+    int64_t n_near = 0;
+    int32_t max_leaf = 0;
+    rbf_level lev[RBF_MAX_DEPTH + 1];
+    rbf_plan *plan[2] = {nullptr, nullptr};  // indexed by rbf_precision
+    // generic device scratch for solver/host-API copies
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int32_t nleaf() const { return lev[D].nbox; }
+    const uint64_t *leaf_key() const { return lev[D].key; }
+};
+
+// tree.cu
+int rbf_scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total_host,
+                           cudaStream_t s);
+int rbf_build_il(rbf_tree *t, int level, cudaStream_t s);
+
+// --------------------------------------------------------------- plan -----
+// Half-spectrum layout of an expansion: dimension 0 keeps k0 = 0..M/2,
+// dimensions 1..d-1 keep k = -M/2..M/2.  The flattened mode index has
+// dimension 0 slowest and dimension d-1 fastest:
+//     m = ((k0 * n1 + k1') * n1 + k2') ...,  k_t' = k_t + M/2.
+// A "row" is (k0, ..., k_{d-2}), a "column" is k_{d-1}.
+struct rbf_plan {
+    int prec = -1;
+    int kernel = -1;
+    double eps = 0, L = 0, alpha = 0;
+    int M = 0, csample = -1;
+    int n0 = 0, n1 = 0;        // values of k0, of k_t (t >= 1)
+    int nrow = 0, ncol = 0;    // rows x cols = modes (ncol = n1, or n0 when d == 1)
+    int64_t nmode = 0;
+    void *omegaC = nullptr;    // [nmode] real: half-spectrum weight * omega * C
+    void *xi = nullptr;        // [n1] real: xi_k, k = -M/2..M/2
+    void *root_ph = nullptr;   // [d][2^D][n1] complex: e^{i xi_k (c_a,t - c_0,t)}
+    void *V[RBF_MAX_DEPTH + 1] = {nullptr};  // expansions per level
+    void *Lleaf = nullptr;     // local expansions at the leaves
+    void *lam_s = nullptr;     // [N] gathered lambda
+    void *u_near = nullptr;    // [N]
+    void *u_far = nullptr;     // [N]
+    size_t bytes = 0;
+};
+
+int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_params *p, int prec,
+                 cudaStream_t s, rbf_plan **out);
+void rbf_plan_free(rbf_plan *p);
+
+// Far-field and near-field passes (expansions.cu, p2p.cu)
+template <typename R>
+int rbf_run_p2p(const rbf_tree *t, int kernel, double eps, const R *lam_s, R *u, cudaStream_t s);
+template <typename R>
+int rbf_run_far(const rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStream_t s);
+
+// Internal product on sorted-order device vectors (FP64 in/out, any arithmetic);
+// used by the matvec entry point and the solver.
+int rbf_matvec_sorted64(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_params *p,
+                        int prec, const double *lam_sorted, double *u_sorted, cudaStream_t s);
+
+void rbf_default_params(rbf_kernel kernel, double side, rbf_fmm_params *p);
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

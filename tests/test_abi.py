@@ -1,0 +1,52 @@
+"""Host-side checks of the C ABI: the library loads and exports every entry point
+declared in include/*.h.  No device work."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        names.update(re.findall(r"^RBF_API\s+[\w\s\*]*?\b(rbf_\w+)\s*\(", src, flags=re.M))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1606_07652_gb300 as rbf
+    from paper_1606_07652_gb300 import build as b
+    b.build()
+    return rbf.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("rbf_tree_build", "rbf_fmm_matvec", "rbf_interp_solve", "rbf_tree_free"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    lib.rbf_strerror.restype = ctypes.c_char_p
+    assert lib.rbf_strerror(0) == b"success"
+    assert lib.rbf_strerror(-1) == b"invalid argument"
+    assert lib.rbf_strerror(-4) == b"iterative solve did not converge"
+
+
+def test_argument_errors_need_no_device(lib):
+    """Null pointers are rejected before any CUDA call."""
+    out = ctypes.c_void_p()
+    assert lib.rbf_tree_build(None, 10, 2, None, 1.0, 2, None, ctypes.byref(out)) == -1
+    assert lib.rbf_fmm_matvec(None, 0, 1.0, None, 0, None, 0, None, 0, 1, None) == -1
+    assert lib.rbf_tree_get_info(None, None) == -1

@@ -1,0 +1,187 @@
+"""GPU parity: the sm_103a library against the FP64 CPU oracle, element by element.
+
+Tree, permutation and lists must be bit-exact.  The FP64 product must match the
+oracle's multilevel FMM to 1e-12 relative L2; the FP32 product is held to a
+stated bound (5e-6 relative L2, about 80 FP32 ulps of accumulated rounding,
+well under the method's own kernel error at these expansion sizes).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 5e-6
+
+
+@pytest.fixture(scope="module")
+def rbf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1606_07652_gb300 as m
+    m.load()
+    return m
+
+
+def _dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _clustered(n, d, seed):
+    rng = np.random.default_rng(seed)
+    means = rng.uniform(0.2, 0.8, (4, d))
+    X = np.clip(means[rng.integers(4, size=n)] + 0.03 * rng.standard_normal((n, d)), 0, 1)
+    return X, rng.standard_normal(n)
+
+
+TREE_CASES = [
+    ("uniform-2d", 2, 5000, 4, "u"),
+    ("uniform-3d-ragged", 3, 7777, 3, "u"),
+    ("clustered-3d-empty-leaves", 3, 6000, 5, "c"),
+    ("faces-2d", 2, 700, 3, "f"),
+    ("depth0", 2, 50, 0, "u"),
+    ("depth1-1d", 1, 300, 1, "u"),
+    ("5d", 5, 3000, 2, "u"),
+]
+
+
+def _points(d, n, kind, seed):
+    if kind == "c":
+        return _clustered(n, d, seed)
+    X, lam = workloads.uniform(n, d, seed)
+    if kind == "f":
+        X[:50] = np.round(X[:50] * 8) / 8  # exactly on box faces
+        X[50] = 1.0
+        X[51] = 0.0
+    return X, lam
+
+
+@pytest.mark.parametrize("name,d,n,D,kind", TREE_CASES)
+def test_tree_bit_exact(rbf, name, d, n, D, kind):
+    X, _ = _points(d, n, kind, seed=len(name))
+    T = O.tree(X, np.zeros(d), 1.0, D)
+    t = rbf.tree_build(_dev(X), lo=np.zeros(d), side=1.0, depth=D)
+    e = t.export()
+    assert np.array_equal(e["perm"], T["perm"])
+    assert np.array_equal(e["keys"], T["keys"])
+    assert np.array_equal(e["leaf_key"], T["leaf_key"])
+    assert np.array_equal(e["leaf_off"], T["leaf_off"])
+    assert np.array_equal(e["near_off"], T["near_off"])
+    assert np.array_equal(e["near_idx"], T["near_idx"])
+    info = t.info()
+    for l in range(D + 1):
+        assert info["n_box"][l] == len(T["levels"][l]["key"])
+    for l in range(2, D + 1):
+        lv = t.export_level(l)
+        assert np.array_equal(lv["key"], T["levels"][l]["key"])
+        assert np.array_equal(lv["il_off"], T["levels"][l]["il_off"])
+        assert np.array_equal(lv["il_idx"], T["levels"][l]["il_idx"])
+
+
+MATVEC_CASES = [
+    # name, d, N, D, kernel, eps, M, L, alpha, kind
+    ("config1", 2, 4096, 3, O.GAUSSIAN, 4.0, 32, 2.5, 0.0, "u"),
+    ("imq-3d-ragged", 3, 9000, 3, O.IMQ, 2.0, 12, 4.0, 4.5, "u"),
+    ("imq-2d-deep", 2, 6000, 5, O.IMQ, 2.0, 16, 4.0, 4.5, "u"),
+    ("gauss-3d-clustered", 3, 5000, 4, O.GAUSSIAN, 3.0, 10, 3.0, 0.0, "c"),
+    ("near-only-depth1", 2, 800, 1, O.IMQ, 2.0, 8, 4.0, 4.5, "u"),
+    ("depth2", 3, 2000, 2, O.GAUSSIAN, 3.0, 12, 3.0, 0.0, "u"),
+    ("1d", 1, 3000, 4, O.IMQ, 3.0, 24, 4.0, 4.5, "u"),
+    ("5d", 5, 1500, 2, O.GAUSSIAN, 1.5, 4, 4.0, 0.0, "u"),
+]
+
+
+@pytest.mark.parametrize("name,d,n,D,kernel,eps,M,L,alpha,kind", MATVEC_CASES)
+def test_matvec_matches_oracle(rbf, name, d, n, D, kernel, eps, M, L, alpha, kind):
+    import torch
+    if name == "config1":
+        X, lam, _ = workloads.config1()
+    else:
+        X, lam = _points(d, n, kind, seed=n)
+    T = O.tree(X, np.zeros(d), 1.0, D)
+    wc = O.coeffs_sampled(kernel, eps, d, M, L, alpha, 1.0)
+    u_ref = O.fmm(T, lam, kernel, eps, wc, M, L)
+    t = rbf.tree_build(_dev(X), lo=np.zeros(d), side=1.0, depth=D)
+    lam_d = _dev(lam)
+    u64 = torch.empty_like(lam_d)
+    rbf.fmm_matvec(t, kernel, eps, lam_d, u64, prec=rbf.FP64, M=M, period_L=L, window_alpha=alpha)
+    u32 = torch.empty_like(lam_d)
+    rbf.fmm_matvec(t, kernel, eps, lam_d, u32, prec=rbf.FP32, M=M, period_L=L, window_alpha=alpha)
+    torch.cuda.synchronize()
+    e64 = rel(u64.cpu().numpy(), u_ref)
+    e32 = rel(u32.cpu().numpy(), u_ref)
+    print(f"{name}: fp64 rel {e64:.3e}  fp32 rel {e32:.3e}")
+    assert e64 <= FP64_TOL
+    assert e32 <= FP32_TOL
+    # a second call reuses the cached plan and must give the same bits
+    u64b = torch.empty_like(lam_d)
+    rbf.fmm_matvec(t, kernel, eps, lam_d, u64b, prec=rbf.FP64, M=M, period_L=L, window_alpha=alpha)
+    assert torch.equal(u64, u64b)
+
+
+def test_closed_form_coefficients_gaussian(rbf):
+    import torch
+    X, lam = workloads.uniform(3000, 2, 9)
+    T = O.tree(X, np.zeros(2), 1.0, 3)
+    wc = O.coeffs_closed_gaussian(4.0, 2, 20, 2.5)
+    u_ref = O.fmm(T, lam, O.GAUSSIAN, 4.0, wc, 20, 2.5)
+    t = rbf.tree_build(_dev(X), lo=np.zeros(2), side=1.0, depth=3)
+    u = torch.empty(len(X), dtype=torch.float64, device="cuda")
+    rbf.fmm_matvec(t, O.GAUSSIAN, 4.0, _dev(lam), u, prec=rbf.FP64, M=20, period_L=2.5,
+                   window_alpha=0.0, csample=0)
+    assert rel(u.cpu().numpy(), u_ref) <= FP64_TOL
+
+
+def test_multiple_rhs_and_host_entry(rbf):
+    import torch
+    X, lam = workloads.uniform(4000, 3, 21)
+    rng = np.random.default_rng(4)
+    lam2 = np.stack([lam, rng.standard_normal(len(X)), rng.standard_normal(len(X))])
+    T = O.tree(X, np.zeros(3), 1.0, 3)
+    wc = O.coeffs_sampled(O.IMQ, 2.0, 3, 10, 4.0, 4.5, 1.0)
+    t = rbf.tree_build(_dev(X), lo=np.zeros(3), side=1.0, depth=3)
+    U = torch.empty(lam2.shape, dtype=torch.float64, device="cuda")
+    rbf.fmm_matvec(t, O.IMQ, 2.0, _dev(lam2), U, prec=rbf.FP64, M=10, period_L=4.0)
+    Uh = rbf.fmm_matvec_host(t, O.IMQ, 2.0, lam2, prec=rbf.FP64, M=10, period_L=4.0)
+    for c in range(3):
+        ref = O.fmm(T, lam2[c], O.IMQ, 2.0, wc, 10, 4.0)
+        assert rel(U[c].cpu().numpy(), ref) <= FP64_TOL
+        assert rel(Uh[c], ref) <= FP64_TOL
+
+
+def test_direct_sum_matches_oracle(rbf):
+    import torch
+    X, lam = workloads.uniform(5000, 3, 2)
+    tg = np.arange(0, 5000, 37)
+    ref = O.direct(X, lam, O.IMQ, 2.0, tg)
+    u = torch.empty(len(tg), dtype=torch.float64, device="cuda")
+    rbf.direct_sum(_dev(X), O.IMQ, 2.0, _dev(lam), _dev(tg.astype(np.int64)), u)
+    assert rel(u.cpu().numpy(), ref) <= 1e-14
+
+
+def test_auto_box_and_bad_arguments(rbf):
+    import torch
+    X, lam = workloads.uniform(1000, 2, 5)
+    X = X * 3.0 - 1.0
+    t = rbf.tree_build(_dev(X), lo=None, depth=-1)
+    info = t.info()
+    assert np.allclose(info["lo"], X.min(axis=0))
+    assert abs(info["side"] - np.max(X.max(axis=0) - X.min(axis=0))) < 1e-15
+    u = torch.empty(1000, dtype=torch.float64, device="cuda")
+    with pytest.raises(rbf.RbfError):
+        rbf.fmm_matvec(t, O.IMQ, 2.0, _dev(lam), u, M=7)          # odd M
+    with pytest.raises(rbf.RbfError):
+        rbf.fmm_matvec(t, O.IMQ, -1.0, _dev(lam), u)              # eps <= 0
+    with pytest.raises(rbf.RbfError):
+        rbf.fmm_matvec(t, O.IMQ, 2.0, _dev(lam), u, M=16, period_L=info["side"])  # L too small
+    with pytest.raises(rbf.RbfError):
+        rbf.fmm_matvec(t, O.IMQ, 2.0, _dev(lam), u, M=16, csample=0)  # closed form is Gaussian-only
