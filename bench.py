@@ -1,0 +1,374 @@
+"""Benchmark of the band-limited FMM product u = A lambda on GB300.
+
+Workload: N = 2^20 centres uniform in [0,1]^3 (seed 1), inverse multiquadric
+Phi(r) = 1/sqrt(1+(eps r)^2), eps = 2, lambda ~ N(0,1), octree depth 5 (32
+points per leaf on average), M = 32 nodes per dimension, period L = 4, taper
+alpha = 4.5.  One step = one full product (gather, near field, P2M, M2M
+upsweep, coupling + downsweep, L2P, scatter) in FP32 arithmetic.  The metric
+is points per second (N / step time).
+
+Default: 1 GPU, 10 timed steps after 3 warm-up steps.  Under torchrun (N > 1)
+every rank runs an independent replica (the product does not shard; weak
+scaling) and rank 0 prints the aggregate over the slowest rank's time.
+
+`--impl reference` times the FP64 CPU oracle instead, on a bounded sample of
+the same workload (the centres of one level-1 box, same tree and expansion
+parameters), and prints its own line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM matvec throughput, 3D N=2^20 IMQ eps=2 (FP32 product)"
+UNIT = "points/s"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "sm_max_mhz": p.get("sm_max_mhz", 2070.0),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x clock."""
+    return N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            with open(self.path) as f:
+                for r in csv.reader(f):
+                    if len(r) >= 9:
+                        rows.append([c.strip() for c in r])
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _traffic(kernel_pass):
+    """DRAM bytes per launch of a pass from the committed ncu summary, if the kernel
+    source has not changed since the counters were taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        tab = json.load(f)
+    ent = tab.get(kernel_pass)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    if not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return ent["bytes_per_launch"] if sha == ent["source_sha"] else None
+
+
+def near_pairs(tree):
+    e = tree.export()
+    n = np.diff(e["leaf_off"])
+    tot = 0
+    for a in range(len(n)):
+        nb = e["near_idx"][e["near_off"][a]:e["near_off"][a + 1]]
+        tot += int(n[a]) * int(n[nb].sum())
+    return tot
+
+
+def run_ours(args):
+    import torch
+    import paper_1606_07652_gb300 as rbf
+    import workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    X, lam, targets, p = workloads.config2()
+    N = len(X)
+    Xd = torch.as_tensor(X, device=dev)
+    ld = torch.as_tensor(lam, device=dev)
+    tree = rbf.tree_build(Xd, lo=np.zeros(3), side=1.0, depth=p["depth"])
+    info = tree.info()
+    kw = dict(M=p["M"], period_L=p["L"], window_alpha=p["alpha"])
+    prec = rbf.FP32
+    u = torch.empty_like(ld)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rbf.fmm_matvec(tree, p["kernel"], p["eps"], ld, u, prec=prec, **kw)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    rbf.profile(tree, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))            # write > L2 between timed steps (untimed)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    prof = rbf.profile_read(tree)
+    rbf.profile(tree, False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = float(np.sum(step_ms))
+    t_max = t_local
+    if dist:
+        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_per_step = t_max / args.steps
+    value = world * N * args.steps / (t_max / 1e3)
+    clocks = clk.summary()
+
+    # end to end through the host entry point: pinned host lambda in, host u out
+    lam_h = torch.as_tensor(lam).pin_memory()
+    u_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    rbf.fmm_matvec_host(tree, p["kernel"], p["eps"], lam_h, u_h, prec=prec, **kw)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rbf.fmm_matvec_host(tree, p["kernel"], p["eps"], lam_h, u_h, prec=prec, **kw)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_t = float(np.sum(e2e_ms))
+    if dist:
+        tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+    e2e = {"value": world * N * args.steps / (e2e_t / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
+
+    out = None
+    if rank == 0:
+        peaks = _peaks()
+        nmode = (p["M"] // 2 + 1) * (p["M"] + 1) ** 2
+        nleaf = info["n_leaf"]
+        passes = {}
+        for name, v in prof.items():
+            if v["launches"]:
+                passes[name] = {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"]}
+        # algorithmic work per launch ("Roofline")
+        flops_p2m = 8.0 * N * nmode
+        bytes_m2l = (2.0 * nleaf + 1.0) * nmode * 8.0
+        pairs = near_pairs(tree)
+        sm_peak_mhz = peaks["sm_max_mhz"]
+        fp32_peak = fp32_peak_tflops(sm_peak_mhz)
+        work = {
+            "p2m": ("alu", flops_p2m / 1e12, fp32_peak, "TFLOP/s"),
+            "l2p": ("alu", flops_p2m / 1e12, fp32_peak, "TFLOP/s"),
+            "m2l": ("hbm", bytes_m2l / 1e9, peaks["hbm_gbs"], "GB/s"),
+            "p2p": ("alu", 11.0 * pairs / 1e12, fp32_peak, "TFLOP/s"),
+        }
+        m2m_bytes = 0.0
+        for l in range(info["depth"]):
+            m2m_bytes += (info["n_box"][l] + info["n_box"][l + 1]) * nmode * 8.0
+        work["m2m"] = ("hbm", m2m_bytes / 1e9, peaks["hbm_gbs"], "GB/s")
+        for name, (bound, amount, peak, unit) in work.items():
+            if name in passes:
+                ms = passes[name]["ms_per_step"]
+                ach = amount / (ms / 1e3)
+                passes[name].update({"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                                     "frac": ach / peak})
+        dom = max((k for k in passes if k in work), key=lambda k: passes[k]["ms_per_step"])
+        d = passes[dom]
+        per_launch_ms = prof[dom]["ms"] / prof[dom]["launches"]
+        launches_per_step = prof[dom]["launches"] / args.steps
+        roof = {"kernel": dom, "bound": d["bound"],
+                "achieved": work[dom][1] / launches_per_step / (per_launch_ms / 1e3),
+                "peak": d["peak"], "unit": d["unit"],
+                "peak_source": ("FP32 FMA peak from unit counts at %g MHz" % sm_peak_mhz
+                                if d["bound"] == "alu" else "of %s HBM copy bandwidth"
+                                % peaks["source"]),
+                "traffic": _traffic(dom)}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        gpu_launches = int(sum(v["launches"] for v in prof.values()))
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32", "data": "synthetic (seeded uniform centres, N(0,1) coefficients)",
+               "config": {"workload": "3D N=2^20 uniform, IMQ eps=2, depth 5, M=32, L=4, alpha=4.5",
+                          "N": N, "d": 3, "depth": info["depth"], "M": p["M"], "modes_per_leaf":
+                          nmode, "n_leaf": nleaf, "near_pairs": pairs,
+                          "parallelism": "replicas" if world > 1 else "single GPU",
+                          "l2": "256 MB buffer written between timed steps"},
+               "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
+               "passes": passes}
+        if not args.skip_extra:
+            out.update(extra_measurements(rbf, tree, Xd, ld, targets, p, kw, dev))
+        if not args.skip_cpu and world == 1:
+            out["cpu_baseline"] = cpu_baseline(X, lam, p, budget_s=args.cpu_budget)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    tree.free()
+    return out
+
+
+def extra_measurements(rbf, tree, Xd, ld, targets, p, kw, dev):
+    """FP64 product throughput and the error of both products against the FP64 direct sum."""
+    import torch
+    N = ld.shape[0]
+    u32 = torch.empty_like(ld)
+    u64 = torch.empty_like(ld)
+    rbf.fmm_matvec(tree, p["kernel"], p["eps"], ld, u32, prec=rbf.FP32, **kw)
+    rbf.fmm_matvec(tree, p["kernel"], p["eps"], ld, u64, prec=rbf.FP64, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rbf.fmm_matvec(tree, p["kernel"], p["eps"], ld, u64, prec=rbf.FP64, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    tg = torch.as_tensor(np.asarray(targets, dtype=np.int64), device=dev)
+    ud = torch.empty(len(targets), dtype=torch.float64, device=dev)
+    rbf.direct_sum(Xd, p["kernel"], p["eps"], ld, tg, ud)
+    torch.cuda.synchronize()
+    ud = ud.cpu().numpy()
+
+    def err(u):
+        v = u.cpu().numpy()[targets]
+        return {"rel_l2": float(np.linalg.norm(v - ud) / np.linalg.norm(ud)),
+                "max_abs": float(np.max(np.abs(v - ud))),
+                "max_rel_to_max": float(np.max(np.abs(v - ud)) / np.max(np.abs(ud)))}
+
+    return {"fp64": {"value": N / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64},
+            "error_vs_direct_4096_targets": {"fp32": err(u32), "fp64": err(u64)}}
+
+
+def _oracle_sample(X, lam, p):
+    """Centres of the level-1 box at the origin (about N/8), same tree and parameters."""
+    k = np.floor(X * 2).astype(np.int64)
+    sel = np.all(k == 0, axis=1)
+    return X[sel], lam[sel]
+
+
+def cpu_baseline(X, lam, p, budget_s=60.0):
+    import oracle as O
+    Xs, ls = _oracle_sample(X, lam, p)
+    t0 = time.perf_counter()
+    T = O.tree(Xs, np.zeros(3), 1.0, p["depth"])
+    wc = O.coeffs_sampled(p["kernel"], p["eps"], 3, p["M"], p["L"], p["alpha"], 1.0)
+    t1 = time.perf_counter()
+    O.fmm(T, ls, p["kernel"], p["eps"], wc, p["M"], p["L"])
+    t2 = time.perf_counter()
+    return {"value": len(Xs) / (t2 - t1), "unit": UNIT, "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle MLFMM product on the {len(Xs)} centres of the level-1 box at "
+                      f"the origin (same root cube, depth 5, M=32, L=4, alpha=4.5); "
+                      f"setup {t1 - t0:.1f} s not timed, product {t2 - t1:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import workloads
+    X, lam, _, p = workloads.config2()
+    vals = []
+    for _ in range(max(args.warmup, 0)):
+        pass  # the oracle has no warm-up state worth paying for
+    for _ in range(args.steps if args.steps <= 2 else 2):
+        vals.append(cpu_baseline(X, lam, p))
+    v = float(np.median([c["value"] for c in vals]))
+    cb = dict(vals[-1])
+    cb["value"] = v
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+            "steps": len(vals), "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded uniform centres, N(0,1) coefficients)",
+            "config": {"workload": "3D N=2^20 uniform, IMQ eps=2, depth 5, M=32, L=4, alpha=4.5",
+                       "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=60.0)
+    args = ap.parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

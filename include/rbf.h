@@ -206,6 +206,24 @@ RBF_API int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps, const r
                      const double *u, double *lambda, int nrhs, const rbf_solve_opts *opts,
                      rbf_solve_report *rep_host, void *stream);
 
+/* Per-pass device timing.  While enabled, every product on the tree records a
+ * pair of CUDA events around each pass, on the stream the pass runs on.
+ * Pass ids: RBF_PASS_P2P near field, RBF_PASS_P2M, RBF_PASS_M2M upsweep,
+ * RBF_PASS_M2L coupling + downsweep, RBF_PASS_L2P, RBF_PASS_PERM gather of
+ * lambda and scatter of u.  rbf_profile(t, 1) enables and clears,
+ * rbf_profile(t, 0) disables.  rbf_profile_read synchronises on the recorded
+ * events and returns, per pass, the summed milliseconds and the number of
+ * kernel launches since the last clear (host arrays of RBF_PASS_COUNT). */
+#define RBF_PASS_P2P 0
+#define RBF_PASS_P2M 1
+#define RBF_PASS_M2M 2
+#define RBF_PASS_M2L 3
+#define RBF_PASS_L2P 4
+#define RBF_PASS_PERM 5
+#define RBF_PASS_COUNT 6
+RBF_API int rbf_profile(rbf_tree *t, int enable);
+RBF_API int rbf_profile_read(rbf_tree *t, double *ms_host, int64_t *launches_host);
+
 /* Release a tree and everything it owns.  NULL is accepted. */
 RBF_API void rbf_tree_free(rbf_tree *t);
 

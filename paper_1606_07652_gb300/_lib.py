@@ -79,6 +79,8 @@ def load():
                                    _c_vp, _c_vp]
     lib.rbf_interp_solve.argtypes = [_c_vp, _c_int, _c_dbl, P(FmmParams), _c_vp, _c_vp, _c_int,
                                      P(SolveOpts), P(SolveReport), _c_vp]
+    lib.rbf_profile.argtypes = [_c_vp, _c_int]
+    lib.rbf_profile_read.argtypes = [_c_vp, _c_vp, _c_vp]
     lib.rbf_tree_free.argtypes = [_c_vp]
     lib.rbf_tree_free.restype = None
     lib.rbf_strerror.argtypes = [_c_int]
@@ -213,19 +215,50 @@ def fmm_matvec(tree: Tree, kernel: int, eps: float, lam, u, prec=FP64, M=None, p
     return u
 
 
-def fmm_matvec_host(tree: Tree, kernel: int, eps: float, lam_host, prec=FP64, M=None,
-                    period_L=None, window_alpha=None, csample=1):
-    """rbf_fmm_matvec_host: numpy float64 in, numpy float64 out (host <-> device inside)."""
-    lam_host = np.ascontiguousarray(lam_host, dtype=np.float64)
-    nrhs = 1 if lam_host.ndim == 1 else lam_host.shape[0]
-    u = np.empty_like(lam_host)
+def _host_ptr(a, where):
+    """Host pointer of a contiguous float64 numpy array or torch CPU tensor (pinned or not)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"{where}: expected a contiguous float64 array")
+        return ctypes.c_void_p(a.ctypes.data)
+    import torch
+    if not isinstance(a, torch.Tensor) or a.is_cuda or a.dtype != torch.float64 \
+            or not a.is_contiguous():
+        raise TypeError(f"{where}: expected a contiguous float64 host tensor")
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def fmm_matvec_host(tree: Tree, kernel: int, eps: float, lam_host, u_host=None, prec=FP64,
+                    M=None, period_L=None, window_alpha=None, csample=1):
+    """rbf_fmm_matvec_host: host float64 in (numpy or torch CPU, e.g. pinned), host out;
+    the host <-> device copies happen inside the call."""
+    if isinstance(lam_host, np.ndarray):
+        lam_host = np.ascontiguousarray(lam_host, dtype=np.float64)
+    if u_host is None:
+        u_host = np.empty(tuple(lam_host.shape), dtype=np.float64)
+    nrhs = 1 if len(lam_host.shape) == 1 else lam_host.shape[0]
     p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"])
     _check(load().rbf_fmm_matvec_host(tree.handle, kernel, float(eps),
                                       ctypes.byref(p) if p is not None else None, prec,
-                                      ctypes.c_void_p(lam_host.ctypes.data),
-                                      ctypes.c_void_p(u.ctypes.data), nrhs, _stream()),
-           "rbf_fmm_matvec_host")
-    return u
+                                      _host_ptr(lam_host, "lam_host"), _host_ptr(u_host, "u_host"),
+                                      nrhs, _stream()), "rbf_fmm_matvec_host")
+    return u_host
+
+
+def profile(tree: Tree, enable: bool = True):
+    """rbf_profile: start (and clear) or stop per-pass event timing."""
+    _check(load().rbf_profile(tree.handle, int(bool(enable))), "rbf_profile")
+
+
+PASS_NAMES = ("p2p", "p2m", "m2m", "m2l", "l2p", "perm")
+
+
+def profile_read(tree: Tree) -> dict:
+    """rbf_profile_read: per pass {"ms": summed milliseconds, "launches": kernel launches}."""
+    ms = (ctypes.c_double * len(PASS_NAMES))()
+    nl = (ctypes.c_int64 * len(PASS_NAMES))()
+    _check(load().rbf_profile_read(tree.handle, ms, nl), "rbf_profile_read")
+    return {n: {"ms": ms[i], "launches": nl[i]} for i, n in enumerate(PASS_NAMES)}
 
 
 def direct_sum(X, kernel: int, eps: float, lam, targets, u):

@@ -2,6 +2,8 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <algorithm>
+
 #include "rbf_internal.cuh"
 
 static thread_local char g_last_error[512] = "";
@@ -50,3 +52,67 @@ extern "C" const char *rbf_strerror(int code)
 extern "C" const char *rbf_last_error(void) { return g_last_error; }
 
 extern "C" const char *rbf_version(void) { return "0.1.0"; }
+
+// ---------------------------------------------------------------- profiling --
+rbf_pass_timer::rbf_pass_timer(rbf_tree *t_, int pass_, cudaStream_t s_, int launches)
+    : t(t_), pass(pass_), s(s_)
+{
+    if (!t || !t->prof.on) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, s);
+    t->prof.start[pass].push_back(e);
+    t->prof.launches[pass] += launches;
+}
+
+rbf_pass_timer::~rbf_pass_timer()
+{
+    if (!t || !t->prof.on) return;
+    if (t->prof.stop[pass].size() >= t->prof.start[pass].size()) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, s);
+    t->prof.stop[pass].push_back(e);
+}
+
+static void prof_clear(rbf_tree *t)
+{
+    for (int p = 0; p < RBF_PASS_COUNT; ++p) {
+        for (cudaEvent_t e : t->prof.start[p]) cudaEventDestroy(e);
+        for (cudaEvent_t e : t->prof.stop[p]) cudaEventDestroy(e);
+        t->prof.start[p].clear();
+        t->prof.stop[p].clear();
+        t->prof.launches[p] = 0;
+    }
+}
+
+void rbf_prof_release(rbf_tree *t) { prof_clear(t); }
+
+extern "C" int rbf_profile(rbf_tree *t, int enable)
+{
+    RBF_REQUIRE(t != nullptr, "rbf_profile: tree is NULL");
+    prof_clear(t);
+    t->prof.on = enable != 0;
+    return RBF_OK;
+}
+
+extern "C" int rbf_profile_read(rbf_tree *t, double *ms, int64_t *launches)
+{
+    RBF_REQUIRE(t != nullptr, "rbf_profile_read: tree is NULL");
+    for (int p = 0; p < RBF_PASS_COUNT; ++p) {
+        double sum = 0.0;
+        const size_t n = std::min(t->prof.start[p].size(), t->prof.stop[p].size());
+        for (size_t q = 0; q < n; ++q) {
+            RBF_CUDA_TRY(cudaEventSynchronize(t->prof.stop[p][q]));
+            float v = 0.0f;
+            RBF_CUDA_TRY(cudaEventElapsedTime(&v, t->prof.start[p][q], t->prof.stop[p][q]));
+            sum += v;
+        }
+        if (ms) ms[p] = sum;
+        if (launches) launches[p] = t->prof.launches[p];
+    }
+    const bool on = t->prof.on;
+    prof_clear(t);
+    t->prof.on = on;
+    return RBF_OK;
+}

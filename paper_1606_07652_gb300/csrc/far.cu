@@ -408,7 +408,7 @@ int dispatch_p2m_l2p(bool l2p, const FarArgs<R> &a, int nleaf, cudaStream_t s)
 }  // namespace
 
 template <typename R>
-int rbf_run_far(const rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStream_t s)
+int rbf_run_far(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStream_t s)
 {
     using C = cplx<R>;
     const int d = t->d, D = t->D;
@@ -437,10 +437,16 @@ int rbf_run_far(const rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, 
     // chunk size: as many points as fit in ~96 KB of phase tables, at most 64
     a.pch = (int)std::max<int64_t>(1, std::min<int64_t>(64, (96 * 1024) / ((int64_t)rowlen * sizeof(C))));
     // P2M at the leaves
-    RBF_TRY(dispatch_p2m_l2p<R>(false, a, nleaf, s));
+    {
+        rbf_pass_timer tm(t, RBF_PASS_P2M, s);
+        RBF_TRY(dispatch_p2m_l2p<R>(false, a, nleaf, s));
+    }
     // M2M up to the root
     const int mb = 256;
     const int mchunks = ceil_div(p->nmode, mb);
+    RBF_REQUIRE(mchunks < 65536, "expansion too large (%lld modes)", (long long)p->nmode);
+    {
+    rbf_pass_timer tm(t, RBF_PASS_M2M, s, D);
     for (int l = D - 1; l >= 0; --l) {
         const double wc = t->side / (double)(1 << (l + 1));
         dim3 grid(t->lev[l].nbox, mchunks);
@@ -449,8 +455,10 @@ int rbf_run_far(const rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, 
                                      (const C *)p->V[l + 1], (C *)p->V[l]);
         RBF_LAUNCH_CHECK();
     }
+    }
     // coupling + downsweep at the leaves
     {
+        rbf_pass_timer tm(t, RBF_PASS_M2L, s);
         const double wD = t->side / (double)(1 << D);
         dim3 grid(nleaf, mchunks);
         k_m2l<R><<<grid, mb, 0, s>>>(d, p->M, D, p->n1, p->nmode, (const R *)p->xi,
@@ -460,10 +468,13 @@ int rbf_run_far(const rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, 
         RBF_LAUNCH_CHECK();
     }
     // L2P
-    RBF_TRY(dispatch_p2m_l2p<R>(true, a, nleaf, s));
+    {
+        rbf_pass_timer tm(t, RBF_PASS_L2P, s);
+        RBF_TRY(dispatch_p2m_l2p<R>(true, a, nleaf, s));
+    }
     return RBF_OK;
 }
 
-template int rbf_run_far<float>(const rbf_tree *, const rbf_plan *, const float *, float *, cudaStream_t);
-template int rbf_run_far<double>(const rbf_tree *, const rbf_plan *, const double *, double *,
+template int rbf_run_far<float>(rbf_tree *, const rbf_plan *, const float *, float *, cudaStream_t);
+template int rbf_run_far<double>(rbf_tree *, const rbf_plan *, const double *, double *,
                                  cudaStream_t);

@@ -28,13 +28,19 @@ int matvec_one(rbf_tree *t, rbf_plan *p, int kernel, double eps, const double *l
 {
     R *lam_s = (R *)p->lam_s, *un = (R *)p->u_near, *uf = (R *)p->u_far;
     const int64_t N = t->N;
-    k_gather<R><<<ceil_div(N, 256), 256, 0, s>>>(lam, perm, N, lam_s);
-    RBF_LAUNCH_CHECK();
+    {
+        rbf_pass_timer tm(t, RBF_PASS_PERM, s);
+        k_gather<R><<<ceil_div(N, 256), 256, 0, s>>>(lam, perm, N, lam_s);
+        RBF_LAUNCH_CHECK();
+    }
     RBF_TRY(rbf_run_p2p<R>(t, kernel, eps, lam_s, un, s));
     const bool far = t->D >= 2;
     if (far) RBF_TRY(rbf_run_far<R>(t, p, lam_s, uf, s));
-    k_scatter<R><<<ceil_div(N, 256), 256, 0, s>>>(un, far ? uf : nullptr, perm, N, u);
-    RBF_LAUNCH_CHECK();
+    {
+        rbf_pass_timer tm(t, RBF_PASS_PERM, s);
+        k_scatter<R><<<ceil_div(N, 256), 256, 0, s>>>(un, far ? uf : nullptr, perm, N, u);
+        RBF_LAUNCH_CHECK();
+    }
     return RBF_OK;
 }
 

@@ -231,8 +231,9 @@ __global__ void __launch_bounds__(DS_THREADS) k_direct(const double *X, int64_t 
 }  // namespace
 
 template <typename R>
-int rbf_run_p2p(const rbf_tree *t, int kernel, double eps, const R *lam_s, R *u, cudaStream_t s)
+int rbf_run_p2p(rbf_tree *t, int kernel, double eps, const R *lam_s, R *u, cudaStream_t s)
 {
+    rbf_pass_timer tm(t, RBF_PASS_P2P, s);
     const R *xs = (const R *)(sizeof(R) == 8 ? (const void *)t->xs64 : (const void *)t->xs32);
     // the FP32 Gaussian goes through exp2, so fold log2(e) into eps^2
     double e2 = eps * eps;
@@ -240,8 +241,8 @@ int rbf_run_p2p(const rbf_tree *t, int kernel, double eps, const R *lam_s, R *u,
     return launch_p2p<R>(t->d, kernel, (R)e2, t, xs, lam_s, u, s);
 }
 
-template int rbf_run_p2p<float>(const rbf_tree *, int, double, const float *, float *, cudaStream_t);
-template int rbf_run_p2p<double>(const rbf_tree *, int, double, const double *, double *,
+template int rbf_run_p2p<float>(rbf_tree *, int, double, const float *, float *, cudaStream_t);
+template int rbf_run_p2p<double>(rbf_tree *, int, double, const double *, double *,
                                  cudaStream_t);
 
 extern "C" int rbf_direct_sum(const double *X, int64_t N, int d, rbf_kernel kernel, double eps,

@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/rbf.h"
 
@@ -106,6 +107,13 @@ struct rbf_level {
 
 struct rbf_plan;  // expansion tables + workspace, one per precision
 
+// Per-pass event timing (rbf_profile); events are recorded only while enabled.
+struct rbf_prof {
+    bool on = false;
+    std::vector<cudaEvent_t> start[RBF_PASS_COUNT], stop[RBF_PASS_COUNT];
+    int64_t launches[RBF_PASS_COUNT] = {0};
+};
+
 struct rbf_tree {
     int64_t N = 0;
     int d = 0, D = 0;
@@ -124,6 +132,7 @@ struct rbf_tree {
     int32_t max_leaf = 0;
     rbf_level lev[RBF_MAX_DEPTH + 1];
     rbf_plan *plan[2] = {nullptr, nullptr};  // indexed by rbf_precision
+    rbf_prof prof;
     // generic device scratch for solver/host-API copies
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -131,10 +140,21 @@ struct rbf_tree {
     const uint64_t *leaf_key() const { return lev[D].key; }
 };
 
+// Records a start event now and a stop event when it goes out of scope, when
+// profiling is on; `launches` kernels are counted for the pass.
+struct rbf_pass_timer {
+    rbf_tree *t;
+    int pass;
+    cudaStream_t s;
+    rbf_pass_timer(rbf_tree *t_, int pass_, cudaStream_t s_, int launches = 1);
+    ~rbf_pass_timer();
+};
+
 // tree.cu
 int rbf_scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total_host,
                            cudaStream_t s);
 int rbf_build_il(rbf_tree *t, int level, cudaStream_t s);
+void rbf_prof_release(rbf_tree *t);
 
 // --------------------------------------------------------------- plan -----
 // Half-spectrum layout of an expansion: dimension 0 keeps k0 = 0..M/2,
@@ -167,9 +187,9 @@ void rbf_plan_free(rbf_plan *p);
 
 // Far-field and near-field passes (expansions.cu, p2p.cu)
 template <typename R>
-int rbf_run_p2p(const rbf_tree *t, int kernel, double eps, const R *lam_s, R *u, cudaStream_t s);
+int rbf_run_p2p(rbf_tree *t, int kernel, double eps, const R *lam_s, R *u, cudaStream_t s);
 template <typename R>
-int rbf_run_far(const rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStream_t s);
+int rbf_run_far(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStream_t s);
 
 // Internal product on sorted-order device vectors (FP64 in/out, any arithmetic);
 // used by the matvec entry point and the solver.

@@ -661,6 +661,7 @@ extern "C" int rbf_tree_export_level(rbf_tree *t, int level, uint64_t *box_key, 
 extern "C" void rbf_tree_free(rbf_tree *t)
 {
     if (!t) return;
+    rbf_prof_release(t);
     rbf_plan_free(t->plan[0]);
     rbf_plan_free(t->plan[1]);
     rbf_free(t->keys);
