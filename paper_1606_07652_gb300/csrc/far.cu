@@ -21,12 +21,22 @@
 
 #include "rbf_internal.cuh"
 
+// tuning knobs of the FP32 P2M/L2P tiles (point-loop unroll, resident CTAs per SM)
+#ifndef RBF_FAR_UNROLL
+#define RBF_FAR_UNROLL 1
+#endif
+#ifndef RBF_FAR_MINB
+#define RBF_FAR_MINB 3
+#endif
+
 namespace {
+
+constexpr int kFarUnroll = RBF_FAR_UNROLL;
 
 template <typename R>
 struct FarArgs {
     int d, M, D, n0, n1, nrow, ncol;
-    int64_t nmode, N;
+    int64_t nmode, mstride, N;   // modes; per-box stride (multiple of 4)
     double lo[RBF_MAX_DIM];
     double side;
     const R *xs;           // SoA [d][N]
@@ -38,6 +48,7 @@ struct FarArgs {
     const cplx<R> *Lx;     // [nleaf][nmode] (L2P in)
     R *u;                  // [N] (L2P out)
     int pch;               // points per shared-memory chunk
+    int seg0, seg;         // table segment lengths (even; seg >= columns read per point)
 };
 
 __device__ __forceinline__ void decode_key(uint64_t key, int d, int l, int *k)
@@ -47,37 +58,62 @@ __device__ __forceinline__ void decode_key(uint64_t key, int d, int l, int *k)
         for (int t = 0; t < d; ++t) k[t] |= (int)((key >> (b * d + t)) & 1u) << b;
 }
 
-// Fill the per-point phase tables of one chunk:
-//   dim 0: E0[p][k0] = s0 * e^{sign i xi_{k0} r_0}, k0 = 0..M/2  (s0 = lambda_p or 1)
-//   dim t>=1: Et[p][j] = e^{sign i xi_{j-M/2} r_t}, j = 0..M
+// Per-point phase tables of one chunk, one segment per dimension, each segment
+// padded to an even number of entries so that pairs of complex values can be
+// read from shared memory with one 16-byte load:
+//   dim 0:    E0[p][k0] = s0 * e^{sign i xi_{k0} r_0}, k0 = 0..M/2  (s0 = lambda_p or 1)
+//   dim t>=1: Et[p][j]  = e^{sign i xi_{j-M/2} r_t}, j = 0..M
+// Padding entries hold zero.
+__host__ __device__ __forceinline__ int even_up(int n) { return (n + 1) & ~1; }
+
 template <typename R>
 __device__ void fill_tables(const FarArgs<R> &a, int64_t p0, int cnt, const double *c,
                             R sign, bool with_lambda, cplx<R> *E)
 {
-    const int rowlen = a.n0 + (a.d - 1) * a.n1;
+    const int seg0 = a.seg0, seg = a.seg;
+    const int rowlen = seg0 + (a.d - 1) * seg;
     for (int idx = threadIdx.x; idx < cnt * rowlen; idx += blockDim.x) {
         int p = idx / rowlen, j = idx - p * rowlen;
         int t, kidx;
-        if (j < a.n0) {
+        bool pad;
+        if (j < seg0) {
             t = 0;
+            pad = j >= a.n0;
             kidx = j + a.M / 2;
         } else {
-            t = 1 + (j - a.n0) / a.n1;
-            kidx = (j - a.n0) % a.n1;
+            t = 1 + (j - seg0) / seg;
+            kidx = (j - seg0) % seg;
+            pad = kidx >= a.n1;
         }
-        R r = a.xs[(int64_t)t * a.N + p0 + p] - (R)c[t];
-        R s, co;
-        sincos_r(sign * a.xi[kidx] * r, &s, &co);
         cplx<R> e;
-        e.x = co;
-        e.y = s;
-        if (t == 0 && with_lambda) {
-            R l = a.lam[p0 + p];
-            e.x *= l;
-            e.y *= l;
+        if (pad) {
+            e.x = e.y = (R)0;
+        } else {
+            R r = a.xs[(int64_t)t * a.N + p0 + p] - (R)c[t];
+            R sn, co;
+            sincos_r(sign * a.xi[kidx] * r, &sn, &co);
+            e.x = co;
+            e.y = sn;
+            if (t == 0 && with_lambda) {
+                R l = a.lam[p0 + p];
+                e.x *= l;
+                e.y *= l;
+            }
         }
         E[idx] = e;
     }
+}
+
+__device__ __forceinline__ void ld2(const float2 *p, float2 &u, float2 &v)
+{
+    const float4 w = *reinterpret_cast<const float4 *>(p);
+    u = make_float2(w.x, w.y);
+    v = make_float2(w.z, w.w);
+}
+__device__ __forceinline__ void ld2(const double2 *p, double2 &u, double2 &v)
+{
+    u = p[0];
+    v = p[1];
 }
 
 __device__ __forceinline__ void leaf_centre(const uint64_t key, int d, int D, const double *lo,
@@ -89,24 +125,69 @@ __device__ __forceinline__ void leaf_centre(const uint64_t key, int d, int D, co
     for (int t = 0; t < d; ++t) c[t] = lo[t] + ((double)k[t] + 0.5) * w;
 }
 
-// row -> (k0 index 0..M/2, k_t index 0..M for 1 <= t < d-1)
-__device__ __forceinline__ void decode_row(int row, int d, int n1, int *kk)
+// Shared-memory offsets of the row factors of one row (k0, k_1, .., k_{d-2}):
+// o[0] = k0 in the dimension-0 segment, o[t] = seg0 + (t-1) seg + k_t.  Kept as
+// scalars so that they stay in registers inside the point loop.
+struct RowOff {
+    int o0, o1, o2, o3, o4;
+};
+
+__device__ __forceinline__ RowOff row_offsets(int row, int d, int n1, int seg0, int seg)
 {
-    for (int t = d - 2; t >= 1; --t) {
-        kk[t] = row % n1;
-        row /= n1;
+    RowOff r;
+    r.o1 = r.o2 = r.o3 = r.o4 = 0;
+    // dimensions d-2 .. 1 are the fastest digits of the row index
+    if (d >= 6) { r.o4 = seg0 + 3 * seg + row % n1; row /= n1; }
+    if (d >= 5) { r.o3 = seg0 + 2 * seg + row % n1; row /= n1; }
+    if (d >= 4) { r.o2 = seg0 + 1 * seg + row % n1; row /= n1; }
+    if (d >= 3) { r.o1 = seg0 + row % n1; row /= n1; }
+    r.o0 = row;
+    return r;
+}
+
+// A_j[row] = E0[p][k0] prod_{1<=t<d-1} Et[p][k_t]  (1 for d == 1)
+template <typename C>
+__device__ __forceinline__ C row_factor(const C *Ep, int d, const RowOff &o)
+{
+    C A;
+    if (d == 1) {
+        A.x = 1;
+        A.y = 0;
+        return A;
     }
-    kk[0] = row;
+    A = Ep[o.o0];
+    if (d >= 3) A = cmul(A, Ep[o.o1]);
+    if (d >= 4) A = cmul(A, Ep[o.o2]);
+    if (d >= 5) A = cmul(A, Ep[o.o3]);
+    if (d >= 6) A = cmul(A, Ep[o.o4]);
+    return A;
 }
 
 // ------------------------------------------------------------------ P2M ---
-template <typename R, int NC>
-__global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) k_p2m(FarArgs<R> a)
+// Thread tile: RPT rows x NCH columns.  The NCE (>= ncol) columns are split in
+// NH halves of NCH = NCE/NH (even) columns; warps alternate halves, so a half
+// is warp-uniform.  Columns >= ncol are padding and are not stored.
+template <int NH>
+__device__ __forceinline__ void tile_coords(int &g, int &h, int &G)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    h = warp % NH;
+    g = (warp / NH) * 32 + lane;
+    G = blockDim.x / NH;
+}
+
+template <typename R, int NCE, int RPT, int NH>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 192 : 256, sizeof(R) == 4 ? RBF_FAR_MINB : 1) k_p2m(FarArgs<R> a)
 {
     using C = cplx<R>;
+    constexpr int NCH = NCE / NH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *E = reinterpret_cast<C *>(smem_raw);
-    const int rowlen = a.n0 + (a.d - 1) * a.n1;
+    const int seg0 = a.seg0, seg = a.seg;
+    const int rowlen = seg0 + (a.d - 1) * seg;
+    const int boff = a.d == 1 ? 0 : seg0 + (a.d - 2) * seg;
+    int g, h, G;
+    tile_coords<NH>(g, h, G);
     const int leaf = blockIdx.x;
     const int64_t p0 = a.leaf_off[leaf];
     const int np = a.leaf_off[leaf + 1] - (int)p0;
@@ -117,14 +198,19 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) k_p2m(FarArgs<R> a
         fill_tables<R>(a, p0, np, c, (R)-1, true, E);
         __syncthreads();
     }
-    for (int row0 = 0; row0 < a.nrow; row0 += blockDim.x) {
-        const int row = row0 + threadIdx.x;
-        const bool active = row < a.nrow;
-        int kk[RBF_MAX_DIM];
-        decode_row(active ? row : 0, a.d, a.n1, kk);
-        C acc[NC];
+    for (int row0 = 0; row0 < a.nrow; row0 += RPT * G) {
+        int rows[RPT];
+        bool act[RPT];
+        RowOff ro[RPT];
+        C acc[RPT][NCH];
 #pragma unroll
-        for (int q = 0; q < NC; ++q) acc[q].x = acc[q].y = (R)0;
+        for (int r = 0; r < RPT; ++r) {
+            rows[r] = row0 + g + r * G;
+            act[r] = rows[r] < a.nrow;
+            ro[r] = row_offsets(act[r] ? rows[r] : 0, a.d, a.n1, seg0, seg);
+#pragma unroll
+            for (int q = 0; q < NCH; ++q) acc[r][q].x = acc[r][q].y = (R)0;
+        }
         for (int ch = 0; ch < nchunk; ++ch) {
             const int cnt = min(a.pch, np - ch * a.pch);
             if (nchunk > 1) {
@@ -132,84 +218,106 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) k_p2m(FarArgs<R> a
                 fill_tables<R>(a, p0 + (int64_t)ch * a.pch, cnt, c, (R)-1, true, E);
                 __syncthreads();
             }
-            if (!active) continue;
+            if (!act[0]) continue;
+#pragma unroll kFarUnroll
             for (int p = 0; p < cnt; ++p) {
                 const C *Ep = E + p * rowlen;
-                C A;
-                const C *B;
-                if (a.d == 1) {
-                    A.x = (R)1;
-                    A.y = (R)0;
-                    B = Ep;
-                } else {
-                    A = Ep[kk[0]];
-                    for (int t = 1; t < a.d - 1; ++t) A = cmul(A, Ep[a.n0 + (t - 1) * a.n1 + kk[t]]);
-                    B = Ep + a.n0 + (a.d - 2) * a.n1;
-                }
+                C A[RPT];
 #pragma unroll
-                for (int q = 0; q < NC; ++q)
-                    if (q < a.ncol) cmac(acc[q], A, B[q]);
+                for (int r = 0; r < RPT; ++r) A[r] = row_factor(Ep, a.d, ro[r]);
+                const C *B = Ep + boff + h * NCH;
+#pragma unroll
+                for (int q = 0; q < NCH; q += 2) {
+                    C b0, b1;
+                    ld2(B + q, b0, b1);
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        cmac(acc[r][q], A[r], b0);
+                        cmac(acc[r][q + 1], A[r], b1);
+                    }
+                }
             }
         }
-        if (active) {
-            C *out = a.V + (int64_t)leaf * a.nmode + (int64_t)row * a.ncol;
 #pragma unroll
-            for (int q = 0; q < NC; ++q)
-                if (q < a.ncol) out[q] = acc[q];
+        for (int r = 0; r < RPT; ++r) {
+            if (!act[r]) continue;
+            C *out = a.V + (int64_t)leaf * a.mstride + (int64_t)rows[r] * a.ncol + h * NCH;
+#pragma unroll
+            for (int q = 0; q < NCH; ++q)
+                if (h * NCH + q < a.ncol) out[q] = acc[r][q];
         }
     }
 }
 
 // ------------------------------------------------------------------ L2P ---
-template <typename R, int NC>
-__global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) k_l2p(FarArgs<R> a)
+template <typename R, int NCE, int RPT, int NH>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 192 : 256, sizeof(R) == 4 ? RBF_FAR_MINB : 1) k_l2p(FarArgs<R> a)
 {
     using C = cplx<R>;
+    constexpr int NCH = NCE / NH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int rowlen = a.n0 + (a.d - 1) * a.n1;
+    const int seg0 = a.seg0, seg = a.seg;
+    const int rowlen = seg0 + (a.d - 1) * seg;
+    const int boff = a.d == 1 ? 0 : seg0 + (a.d - 2) * seg;
     C *E = reinterpret_cast<C *>(smem_raw);
     R *part = reinterpret_cast<R *>(E + (size_t)a.pch * rowlen);  // [nwarp][pch]
     const int nwarp = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int g, h, G;
+    tile_coords<NH>(g, h, G);
     const int leaf = blockIdx.x;
     const int64_t p0 = a.leaf_off[leaf];
     const int np = a.leaf_off[leaf + 1] - (int)p0;
     double c[RBF_MAX_DIM];
     leaf_centre(a.leaf_key[leaf], a.d, a.D, a.lo, a.side, c);
-    const C *Lleaf = a.Lx + (int64_t)leaf * a.nmode;
+    const C *Lleaf = a.Lx + (int64_t)leaf * a.mstride;
     for (int ch0 = 0; ch0 < np; ch0 += a.pch) {
         const int cnt = min(a.pch, np - ch0);
         __syncthreads();
         fill_tables<R>(a, p0 + ch0, cnt, c, (R)1, false, E);
         for (int q = threadIdx.x; q < nwarp * a.pch; q += blockDim.x) part[q] = (R)0;
         __syncthreads();
-        for (int row0 = 0; row0 < a.nrow; row0 += blockDim.x) {
-            const int row = row0 + threadIdx.x;
-            const bool active = row < a.nrow;
-            int kk[RBF_MAX_DIM];
-            decode_row(active ? row : 0, a.d, a.n1, kk);
-            C Lr[NC];
+        for (int row0 = 0; row0 < a.nrow; row0 += RPT * G) {
+            RowOff ro[RPT];
+            C Lr[RPT][NCH];
 #pragma unroll
-            for (int q = 0; q < NC; ++q) {
-                if (active && q < a.ncol) Lr[q] = Lleaf[(int64_t)row * a.ncol + q];
-                else Lr[q].x = Lr[q].y = (R)0;
+            for (int r = 0; r < RPT; ++r) {
+                const int row = row0 + g + r * G;
+                const bool act = row < a.nrow;
+                ro[r] = row_offsets(act ? row : 0, a.d, a.n1, seg0, seg);
+#pragma unroll
+                for (int q = 0; q < NCH; ++q) {
+                    const int col = h * NCH + q;
+                    if (act && col < a.ncol) Lr[r][q] = Lleaf[(int64_t)row * a.ncol + col];
+                    else Lr[r][q].x = Lr[r][q].y = (R)0;
+                }
             }
+#pragma unroll kFarUnroll
             for (int p = 0; p < cnt; ++p) {
                 const C *Ep = E + p * rowlen;
-                C P;
-                P.x = P.y = (R)0;
-                const C *B = (a.d == 1) ? Ep : Ep + a.n0 + (a.d - 2) * a.n1;
+                const C *B = Ep + boff + h * NCH;
+                C P[RPT];
 #pragma unroll
-                for (int q = 0; q < NC; ++q)
-                    if (q < a.ncol) cmac(P, Lr[q], B[q]);
-                R v;
-                if (a.d == 1) {
-                    v = P.x;
-                } else {
-                    C A = Ep[kk[0]];
-                    for (int t = 1; t < a.d - 1; ++t) A = cmul(A, Ep[a.n0 + (t - 1) * a.n1 + kk[t]]);
-                    v = A.x * P.x - A.y * P.y;
+                for (int r = 0; r < RPT; ++r) P[r].x = P[r].y = (R)0;
+#pragma unroll
+                for (int q = 0; q < NCH; q += 2) {
+                    C b0, b1;
+                    ld2(B + q, b0, b1);
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        cmac(P[r], Lr[r][q], b0);
+                        cmac(P[r], Lr[r][q + 1], b1);
+                    }
                 }
-                if (!active) v = (R)0;
+                R v = (R)0;
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    if (a.d == 1) {
+                        v += P[r].x;
+                    } else {
+                        const C A = row_factor(Ep, a.d, ro[r]);
+                        v += A.x * P[r].x - A.y * P[r].y;
+                    }
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (lane == 0) part[warp * a.pch + p] += v;
@@ -217,9 +325,9 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) k_l2p(FarArgs<R> a
         }
         __syncthreads();
         for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-            R s = (R)0;
-            for (int w = 0; w < nwarp; ++w) s += part[w * a.pch + p];
-            a.u[p0 + ch0 + p] = s;
+            R sum = (R)0;
+            for (int w = 0; w < nwarp; ++w) sum += part[w * a.pch + p];
+            a.u[p0 + ch0 + p] = sum;
         }
     }
 }
@@ -227,7 +335,7 @@ __global__ void __launch_bounds__(sizeof(R) == 8 ? 256 : 512) k_l2p(FarArgs<R> a
 // ------------------------------------------------------------------ M2M ---
 // Parents at level l from their children at level l+1 (child width wc).
 template <typename R>
-__global__ void k_m2m(int d, int M, int n1, int64_t nmode, const R *xi, double wc,
+__global__ void k_m2m(int d, int M, int n1, int64_t nmode, int64_t ms, const R *xi, double wc,
                       const int32_t *child_off, const uint64_t *child_key, const cplx<R> *Vc,
                       cplx<R> *Vp)
 {
@@ -258,9 +366,9 @@ __global__ void k_m2m(int d, int M, int n1, int64_t nmode, const R *xi, double w
         const unsigned bits = (unsigned)(child_key[cidx] & ((1u << d) - 1u));
         C ph = (bits & 1u) ? P[0] : cconj(P[0]);
         for (int t = 1; t < d; ++t) ph = cmul(ph, ((bits >> t) & 1u) ? P[t] : cconj(P[t]));
-        cmac(acc, ph, Vc[(int64_t)cidx * nmode + m]);
+        cmac(acc, ph, Vc[(int64_t)cidx * ms + m]);
     }
-    Vp[(int64_t)p * nmode + m] = acc;
+    Vp[(int64_t)p * ms + m] = acc;
 }
 
 // ------------------------------------------------------------------ M2L ---
@@ -268,7 +376,7 @@ __global__ void k_m2m(int d, int M, int n1, int64_t nmode, const R *xi, double w
 // neighbours of the leaf are placed on their 3^d offset grid in shared memory
 // and the offset phases are summed one dimension at a time.
 template <typename R>
-__global__ void k_m2l(int d, int M, int D, int n1, int64_t nmode, const R *xi, const R *omegaC,
+__global__ void k_m2l(int d, int M, int D, int n1, int64_t nmode, int64_t ms, const R *xi, const R *omegaC,
                       double wD, const cplx<R> *root_ph, const uint64_t *leaf_key,
                       const int32_t *near_off, const int32_t *near_idx, const cplx<R> *V0,
                       const cplx<R> *VD, cplx<R> *Lx)
@@ -328,12 +436,12 @@ __global__ void k_m2l(int d, int M, int D, int n1, int64_t nmode, const R *xi, c
         C inner;
         inner.x = inner.y = (R)0;
         if (bz >= 0) {
-            C v = VD[(int64_t)bz * nmode + m];
+            C v = VD[(int64_t)bz * ms + m];
             inner.x += v.x;
             inner.y += v.y;
         }
-        if (bp >= 0) cmac(inner, Q[tl], VD[(int64_t)bp * nmode + m]);
-        if (bm >= 0) cmac(inner, cconj(Q[tl]), VD[(int64_t)bm * nmode + m]);
+        if (bp >= 0) cmac(inner, Q[tl], VD[(int64_t)bp * ms + m]);
+        if (bm >= 0) cmac(inner, cconj(Q[tl]), VD[(int64_t)bm * ms + m]);
         // factor of the other dimensions
         int gg = g;
         C f;
@@ -353,17 +461,166 @@ __global__ void k_m2l(int d, int M, int D, int n1, int64_t nmode, const R *xi, c
     C out;
     out.x = w * acc.x;
     out.y = w * acc.y;
-    Lx[(int64_t)a * nmode + m] = out;
+    Lx[(int64_t)a * ms + m] = out;
 }
 
-template <typename R>
-int pick_block(int nrow)
+// Grouped coupling + downsweep for d <= 3: one CTA per level-(D-1) box P and a
+// chunk of modes.  The 2^d children of P are the targets; their neighbour
+// leaves all lie in the 4^d block of leaves around P (block coordinate
+// i_t = k_t - 2 P_t + 1).  For one mode (one thread) the 3^d stencil
+//     S_a = sum_{delta in {-1,0,1}^d} prod_t Q_t^{delta_t} V_{a+delta},  Q_t = e^{-i xi_t w_D}
+// is summed one dimension at a time over the block, so each neighbour
+// expansion is read once per CTA instead of once per target.
+template <typename R, int DIM>
+__global__ void __launch_bounds__(128) k_m2l_grp(int M, int D, int n1, int64_t nmode, int64_t ms,
+                                                 const R *xi,
+                                                 const R *omegaC, double wD, const cplx<R> *root_ph,
+                                                 const uint64_t *parent_key, const int32_t *nb4,
+                                                 const cplx<R> *V0, const cplx<R> *VD, cplx<R> *Lx)
 {
-    const int bmax = sizeof(R) == 8 ? 256 : 512;
-    int best = 128, best_waste = 1 << 30;
-    for (int bd = 128; bd <= bmax; bd += 32) {
-        int passes = (nrow + bd - 1) / bd;
-        int waste = passes * bd - nrow;
+    using C = cplx<R>;
+    constexpr int NB = DIM == 1 ? 4 : (DIM == 2 ? 16 : 64);
+    __shared__ int32_t nb[NB];
+    const int p = blockIdx.x;
+    for (int q = threadIdx.x; q < NB; q += blockDim.x) nb[q] = nb4[(int64_t)p * NB + q];
+    __syncthreads();
+    const int64_t m = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    if (m >= nmode) return;
+    int kidx[3] = {0, 0, 0};
+    {
+        int64_t r = m;
+        for (int t = DIM - 1; t >= 1; --t) {
+            kidx[t] = (int)(r % n1);
+            r /= n1;
+        }
+        kidx[0] = (int)r + M / 2;
+    }
+    C Q[3];
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+        R sn, cs;
+        sincos_r(-xi[kidx[t]] * (R)wD, &sn, &cs);
+        Q[t].x = cs;
+        Q[t].y = sn;
+    }
+    auto ld = [&](int pos) -> C {
+        const int b = nb[pos];
+        if (b >= 0) return VD[(int64_t)b * ms + m];
+        C z;
+        z.x = z.y = (R)0;
+        return z;
+    };
+    // 3-tap sum for targets at block positions 1 and 2 of a line v[0..3]
+    auto tap = [&](const C *v, C q, C *out) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            C s = v[j + 1];
+            cmac(s, cconj(q), v[j]);
+            cmac(s, q, v[j + 2]);
+            out[j] = s;
+        }
+    };
+    C S[8];  // targets, index j0 + 2 j1 + 4 j2 (j_t = 0, 1 <-> block position 1, 2)
+    if (DIM == 1) {
+        C v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = ld(i);
+        tap(v, Q[0], S);
+    } else if (DIM == 2) {
+        C s1[4][2];  // [i1][j0]
+#pragma unroll
+        for (int i1 = 0; i1 < 4; ++i1) {
+            C v[4];
+#pragma unroll
+            for (int i0 = 0; i0 < 4; ++i0) v[i0] = ld(i0 + 4 * i1);
+            tap(v, Q[0], s1[i1]);
+        }
+#pragma unroll
+        for (int j0 = 0; j0 < 2; ++j0) {
+            C v[4], o[2];
+#pragma unroll
+            for (int i1 = 0; i1 < 4; ++i1) v[i1] = s1[i1][j0];
+            tap(v, Q[1], o);
+            S[j0] = o[0];
+            S[j0 + 2] = o[1];
+        }
+    } else {
+        C s2[4][2][2];  // [i2][j1][j0]
+#pragma unroll
+        for (int i2 = 0; i2 < 4; ++i2) {
+            C s1[4][2];  // [i1][j0]
+#pragma unroll
+            for (int i1 = 0; i1 < 4; ++i1) {
+                C v[4];
+#pragma unroll
+                for (int i0 = 0; i0 < 4; ++i0) v[i0] = ld(i0 + 4 * i1 + 16 * i2);
+                tap(v, Q[0], s1[i1]);
+            }
+#pragma unroll
+            for (int j0 = 0; j0 < 2; ++j0) {
+                C v[4], o[2];
+#pragma unroll
+                for (int i1 = 0; i1 < 4; ++i1) v[i1] = s1[i1][j0];
+                tap(v, Q[1], o);
+                s2[i2][0][j0] = o[0];
+                s2[i2][1][j0] = o[1];
+            }
+        }
+#pragma unroll
+        for (int j1 = 0; j1 < 2; ++j1)
+#pragma unroll
+            for (int j0 = 0; j0 < 2; ++j0) {
+                C v[4], o[2];
+#pragma unroll
+                for (int i2 = 0; i2 < 4; ++i2) v[i2] = s2[i2][j1][j0];
+                tap(v, Q[2], o);
+                S[j0 + 2 * j1] = o[0];
+                S[j0 + 2 * j1 + 4] = o[1];
+            }
+    }
+    // targets: L_a = omega C (e^{i xi.(c_a - c_0)} V_0 - S_a)
+    int kp[3] = {0, 0, 0};
+    {
+        const uint64_t key = parent_key[p];
+        for (int b = 0; b < D - 1; ++b)
+#pragma unroll
+            for (int t = 0; t < DIM; ++t) kp[t] |= (int)((key >> (b * DIM + t)) & 1u) << b;
+    }
+    const int64_t nk = (int64_t)1 << D;
+    C rp[3][2];
+#pragma unroll
+    for (int t = 0; t < DIM; ++t)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) rp[t][j] = root_ph[((int64_t)t * nk + 2 * kp[t] + j) * n1 + kidx[t]];
+    const C v0 = V0[m];
+    const R w = omegaC[m];
+#pragma unroll
+    for (int c = 0; c < (1 << DIM); ++c) {
+        int pos = 0;
+#pragma unroll
+        for (int t = 0; t < DIM; ++t) pos += (((c >> t) & 1) + 1) << (2 * t);
+        const int a = nb[pos];
+        if (a < 0) continue;
+        C ph = rp[0][c & 1];
+#pragma unroll
+        for (int t = 1; t < DIM; ++t) ph = cmul(ph, rp[t][(c >> t) & 1]);
+        C r = cmul(ph, v0);
+        C out;
+        out.x = w * (r.x - S[c].x);
+        out.y = w * (r.y - S[c].y);
+        Lx[(int64_t)a * ms + m] = out;
+    }
+}
+
+// block size: multiple of 32*NH threads, fewest idle row slots
+inline int pick_block(int nrow, int rpt, int nh, int bmax)
+{
+    int best = 64, best_waste = 1 << 30;
+    for (int bd = 64; bd <= bmax; bd += 32 * nh) {
+        if (bd % (32 * nh)) continue;
+        const int per = (bd / nh) * rpt;
+        const int passes = (nrow + per - 1) / per;
+        const int waste = passes * per - nrow;
         if (waste < best_waste || (waste == best_waste && bd > best)) {
             best = bd;
             best_waste = waste;
@@ -372,21 +629,30 @@ int pick_block(int nrow)
     return best;
 }
 
-template <typename R, int NC>
-int launch_p2m_l2p(bool l2p, const FarArgs<R> &a, int nleaf, cudaStream_t s)
+template <typename R, int NCE>
+int launch_p2m_l2p(bool l2p, const FarArgs<R> &a0, int nleaf, cudaStream_t s)
 {
-    const int bd = pick_block<R>(a.nrow);
-    const int rowlen = a.n0 + (a.d - 1) * a.n1;
+    constexpr int RPT = sizeof(R) == 4 ? 2 : 1;
+    constexpr int NH = sizeof(R) == 4 ? 2 : 1;
+    static_assert(NCE % (2 * NH) == 0, "column halves must be even");
+    // the column segment is read NCE entries wide; all segments of dims >= 1
+    // share its length, and dim 0 is the column segment when d == 1
+    FarArgs<R> a = a0;
+    a.seg = NCE;
+    a.seg0 = a.d == 1 ? NCE : even_up(a.n0);
+    const int rowlen = a.seg0 + (a.d - 1) * a.seg;
+    a.pch = (int)std::max<int64_t>(1, std::min<int64_t>(64, (64 * 1024) / ((int64_t)rowlen * sizeof(cplx<R>))));
+    const int bd = pick_block(a.nrow, RPT, NH, sizeof(R) == 4 ? 192 : 256);
     size_t smem = (size_t)a.pch * rowlen * sizeof(cplx<R>);
     if (l2p) smem += (size_t)(bd / 32) * a.pch * sizeof(R);
     if (l2p) {
-        RBF_CUDA_TRY(cudaFuncSetAttribute(k_l2p<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-        k_l2p<R, NC><<<nleaf, bd, smem, s>>>(a);
+        RBF_CUDA_TRY(cudaFuncSetAttribute(k_l2p<R, NCE, RPT, NH>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_l2p<R, NCE, RPT, NH><<<nleaf, bd, smem, s>>>(a);
     } else {
-        RBF_CUDA_TRY(cudaFuncSetAttribute(k_p2m<R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-        k_p2m<R, NC><<<nleaf, bd, smem, s>>>(a);
+        RBF_CUDA_TRY(cudaFuncSetAttribute(k_p2m<R, NCE, RPT, NH>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_p2m<R, NCE, RPT, NH><<<nleaf, bd, smem, s>>>(a);
     }
     RBF_LAUNCH_CHECK();
     return RBF_OK;
@@ -396,13 +662,14 @@ template <typename R>
 int dispatch_p2m_l2p(bool l2p, const FarArgs<R> &a, int nleaf, cudaStream_t s)
 {
     const int nc = a.ncol;
-    if (nc <= 9) return launch_p2m_l2p<R, 9>(l2p, a, nleaf, s);
-    if (nc <= 17) return launch_p2m_l2p<R, 17>(l2p, a, nleaf, s);
-    if (nc <= 25) return launch_p2m_l2p<R, 25>(l2p, a, nleaf, s);
-    if (nc <= 33) return launch_p2m_l2p<R, 33>(l2p, a, nleaf, s);
-    if (nc <= 41) return launch_p2m_l2p<R, 41>(l2p, a, nleaf, s);
-    if (nc <= 49) return launch_p2m_l2p<R, 49>(l2p, a, nleaf, s);
-    return launch_p2m_l2p<R, 65>(l2p, a, nleaf, s);
+    // FP32 splits the columns in two even halves: widths are multiples of 4
+    if (nc <= 12) return launch_p2m_l2p<R, 12>(l2p, a, nleaf, s);
+    if (nc <= 20) return launch_p2m_l2p<R, 20>(l2p, a, nleaf, s);
+    if (nc <= 28) return launch_p2m_l2p<R, 28>(l2p, a, nleaf, s);
+    if (nc <= 36) return launch_p2m_l2p<R, 36>(l2p, a, nleaf, s);
+    if (nc <= 44) return launch_p2m_l2p<R, 44>(l2p, a, nleaf, s);
+    if (nc <= 52) return launch_p2m_l2p<R, 52>(l2p, a, nleaf, s);
+    return launch_p2m_l2p<R, 68>(l2p, a, nleaf, s);
 }
 
 }  // namespace
@@ -422,6 +689,7 @@ int rbf_run_far(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaSt
     a.nrow = p->nrow;
     a.ncol = p->ncol;
     a.nmode = p->nmode;
+    a.mstride = p->mstride;
     a.N = t->N;
     for (int q = 0; q < RBF_MAX_DIM; ++q) a.lo[q] = t->lo[q];
     a.side = t->side;
@@ -433,9 +701,8 @@ int rbf_run_far(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaSt
     a.V = (C *)p->V[D];
     a.Lx = (const C *)p->Lleaf;
     a.u = u_far;
-    const int rowlen = a.n0 + (d - 1) * a.n1;
-    // chunk size: as many points as fit in ~96 KB of phase tables, at most 64
-    a.pch = (int)std::max<int64_t>(1, std::min<int64_t>(64, (96 * 1024) / ((int64_t)rowlen * sizeof(C))));
+    a.pch = 0;   // set per launch: as many points as fit in ~64 KB of tables, at most 64
+    a.seg0 = a.seg = 0;
     // P2M at the leaves
     {
         rbf_pass_timer tm(t, RBF_PASS_P2M, s);
@@ -450,18 +717,33 @@ int rbf_run_far(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaSt
     for (int l = D - 1; l >= 0; --l) {
         const double wc = t->side / (double)(1 << (l + 1));
         dim3 grid(t->lev[l].nbox, mchunks);
-        k_m2m<R><<<grid, mb, 0, s>>>(d, p->M, p->n1, p->nmode, (const R *)p->xi, wc,
+        k_m2m<R><<<grid, mb, 0, s>>>(d, p->M, p->n1, p->nmode, p->mstride, (const R *)p->xi, wc,
                                      t->lev[l].child_off, t->lev[l + 1].key,
                                      (const C *)p->V[l + 1], (C *)p->V[l]);
         RBF_LAUNCH_CHECK();
     }
     }
     // coupling + downsweep at the leaves
-    {
+    if (d <= 3) {
+        rbf_pass_timer tm(t, RBF_PASS_M2L, s);
+        const double wD = t->side / (double)(1 << D);
+        const int gb = 128;
+        dim3 grid(t->lev[D - 1].nbox, ceil_div(p->nmode, gb));
+        const C *V0 = (const C *)p->V[0], *VD = (const C *)p->V[D];
+#define RBF_M2L_GRP(DD)                                                                            \
+    k_m2l_grp<R, DD><<<grid, gb, 0, s>>>(p->M, D, p->n1, p->nmode, p->mstride, (const R *)p->xi,   \
+                                         (const R *)p->omegaC, wD, (const C *)p->root_ph,           \
+                                         t->lev[D - 1].key, t->nb4, V0, VD, (C *)p->Lleaf)
+        if (d == 1) RBF_M2L_GRP(1);
+        else if (d == 2) RBF_M2L_GRP(2);
+        else RBF_M2L_GRP(3);
+#undef RBF_M2L_GRP
+        RBF_LAUNCH_CHECK();
+    } else {
         rbf_pass_timer tm(t, RBF_PASS_M2L, s);
         const double wD = t->side / (double)(1 << D);
         dim3 grid(nleaf, mchunks);
-        k_m2l<R><<<grid, mb, 0, s>>>(d, p->M, D, p->n1, p->nmode, (const R *)p->xi,
+        k_m2l<R><<<grid, mb, 0, s>>>(d, p->M, D, p->n1, p->nmode, p->mstride, (const R *)p->xi,
                                      (const R *)p->omegaC, wD, (const C *)p->root_ph, t->leaf_key(),
                                      t->near_off, t->near_idx, (const C *)p->V[0],
                                      (const C *)p->V[D], (C *)p->Lleaf);

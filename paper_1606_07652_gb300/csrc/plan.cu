@@ -223,8 +223,8 @@ template <typename R>
 static int alloc_work(rbf_tree *t, rbf_plan *p)
 {
     for (int l = 0; l <= t->D; ++l)
-        RBF_TRY(rbf_alloc(reinterpret_cast<cplx<R> **>(&p->V[l]), (size_t)t->lev[l].nbox * p->nmode));
-    RBF_TRY(rbf_alloc(reinterpret_cast<cplx<R> **>(&p->Lleaf), (size_t)t->nleaf() * p->nmode));
+        RBF_TRY(rbf_alloc(reinterpret_cast<cplx<R> **>(&p->V[l]), (size_t)t->lev[l].nbox * p->mstride));
+    RBF_TRY(rbf_alloc(reinterpret_cast<cplx<R> **>(&p->Lleaf), (size_t)t->nleaf() * p->mstride));
     RBF_TRY(rbf_alloc(reinterpret_cast<R **>(&p->lam_s), t->N));
     RBF_TRY(rbf_alloc(reinterpret_cast<R **>(&p->u_near), t->N));
     RBF_TRY(rbf_alloc(reinterpret_cast<R **>(&p->u_far), t->N));
@@ -280,6 +280,7 @@ int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_param
     p->n0 = M / 2 + 1;
     p->n1 = M + 1;
     p->nmode = nmode;
+    p->mstride = (nmode + 3) & ~(int64_t)3;
     if (d == 1) {
         p->nrow = 1;
         p->ncol = p->n0;

@@ -130,6 +130,7 @@ struct rbf_tree {
     int32_t *near_idx = nullptr;    // [n_near]
     int64_t n_near = 0;
     int32_t max_leaf = 0;
+    int32_t *nb4 = nullptr;         // [nbox(D-1)][4^d] leaf ids around each parent (d <= 3)
     rbf_level lev[RBF_MAX_DEPTH + 1];
     rbf_plan *plan[2] = {nullptr, nullptr};  // indexed by rbf_precision
     rbf_prof prof;
@@ -170,6 +171,7 @@ struct rbf_plan {
     int n0 = 0, n1 = 0;        // values of k0, of k_t (t >= 1)
     int nrow = 0, ncol = 0;    // rows x cols = modes (ncol = n1, or n0 when d == 1)
     int64_t nmode = 0;
+    int64_t mstride = 0;       // per-box stride of an expansion array (multiple of 4)
     void *omegaC = nullptr;    // [nmode] real: half-spectrum weight * omega * C
     void *xi = nullptr;        // [n1] real: xi_k, k = -M/2..M/2
     void *root_ph = nullptr;   // [d][2^D][n1] complex: e^{i xi_k (c_a,t - c_0,t)}

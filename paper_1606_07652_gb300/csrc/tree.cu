@@ -335,6 +335,28 @@ __global__ void k_i32_to_i64(const int32_t *in, int64_t *out, int64_t n)
     if (i < n) out[i] = in[i];
 }
 
+// 4^d block of leaves around each level-(D-1) box P: block coordinate i_t
+// covers leaf coordinate 2 P_t - 1 + i_t; -1 marks an empty or outside leaf.
+__global__ void k_nb4(const uint64_t *pkey, int32_t np, const uint64_t *leaf_key, int32_t nleaf,
+                      int d, int D, int32_t *nb4)
+{
+    int nb = 1;
+    for (int t = 0; t < d; ++t) nb *= 4;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)np * nb) return;
+    int32_t p = (int32_t)(i / nb);
+    int pos = (int)(i % nb);
+    int64_t kp[RBF_MAX_DIM], kl[RBF_MAX_DIM];
+    morton_decode(pkey[p], d, D - 1, kp);
+    const int64_t kmax = ((int64_t)1 << D) - 1;
+    bool inside = true;
+    for (int t = 0; t < d; ++t) {
+        kl[t] = 2 * kp[t] - 1 + ((pos >> (2 * t)) & 3);
+        inside = inside && kl[t] >= 0 && kl[t] <= kmax;
+    }
+    nb4[i] = inside ? find_key(leaf_key, nleaf, morton_encode(kl, d, D)) : -1;
+}
+
 }  // namespace
 
 // ----------------------------------------------------------- host side ----
@@ -493,6 +515,14 @@ static int build_impl(rbf_tree *t, const double *X, cudaStream_t s)
     k_near<true><<<ceil_div(nleaf, 128), 128, 0, s>>>(t->lev[D].key, nleaf, d, D, nullptr,
                                                      t->near_off, t->near_idx);
     RBF_LAUNCH_CHECK();
+    if (D >= 2 && d <= 3) {
+        const int32_t np = t->lev[D - 1].nbox;
+        const int64_t n = (int64_t)np << (2 * d);
+        RBF_TRY(rbf_alloc(&t->nb4, n));
+        k_nb4<<<ceil_div(n, 256), 256, 0, s>>>(t->lev[D - 1].key, np, t->lev[D].key, nleaf, d, D,
+                                              t->nb4);
+        RBF_LAUNCH_CHECK();
+    }
     RBF_CUDA_TRY(cudaStreamSynchronize(s));
     rbf_free(cnt);
     return RBF_OK;
@@ -671,6 +701,7 @@ extern "C" void rbf_tree_free(rbf_tree *t)
     rbf_free(t->leaf_off);
     rbf_free(t->near_off);
     rbf_free(t->near_idx);
+    rbf_free(t->nb4);
     for (int l = 0; l <= RBF_MAX_DEPTH; ++l) {
         rbf_free(t->lev[l].key);
         rbf_free(t->lev[l].parent);
