@@ -64,7 +64,9 @@ typedef enum { RBF_FP64 = 0, RBF_FP32 = 1 } rbf_precision;
  *  M            quadrature nodes per dimension (even, 2..64).  The nodes are
  *               xi_k = k * 2pi/L, k = -M/2..M/2, with half weight at +-M/2,
  *               so the band limit is sigma = pi M / L.
- *  period_L     period of the sampled kernel; must exceed twice the root side.
+ *  period_L     period of the sampled kernel; must exceed the root side (twice
+ *               the root side when window_alpha > 0).  Far offsets have
+ *               components below `side`, so Phi(L - side) bounds the image error.
  *  window_alpha steepness of the erfc taper applied to slowly decaying kernels
  *               before periodisation (0 = no taper).  The taper is flat on
  *               |t| <= side and falls to ~0 at |t| = L - side.

@@ -242,9 +242,12 @@ int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_param
     RBF_REQUIRE(kernel == RBF_GAUSSIAN || kernel == RBF_IMQ, "unknown kernel %d", (int)kernel);
     RBF_REQUIRE(eps > 0.0 && std::isfinite(eps), "eps must be positive and finite");
     RBF_REQUIRE(pp->M >= 2 && pp->M <= 64 && pp->M % 2 == 0, "M=%d must be even in [2, 64]", pp->M);
-    RBF_REQUIRE(pp->period_L > 2.0 * t->side, "period_L=%g must exceed twice the root side %g",
-                pp->period_L, t->side);
     RBF_REQUIRE(pp->window_alpha >= 0.0, "window_alpha must be >= 0");
+    // far offsets reach |r_t| < side: the nearest image sits at >= L - side, and
+    // the taper needs a transition zone L - 2 side > 0
+    RBF_REQUIRE(pp->period_L > (pp->window_alpha > 0.0 ? 2.0 : 1.0) * t->side,
+                "period_L=%g must exceed %s the root side %g", pp->period_L,
+                pp->window_alpha > 0.0 ? "twice" : "", t->side);
     RBF_REQUIRE(pp->csample == 0 || pp->csample == 1, "csample must be 0 or 1");
     RBF_REQUIRE(pp->csample == 1 || kernel == RBF_GAUSSIAN,
                 "closed-form coefficients exist for the Gaussian only");

@@ -182,6 +182,6 @@ def test_auto_box_and_bad_arguments(rbf):
     with pytest.raises(rbf.RbfError):
         rbf.fmm_matvec(t, O.IMQ, -1.0, _dev(lam), u)              # eps <= 0
     with pytest.raises(rbf.RbfError):
-        rbf.fmm_matvec(t, O.IMQ, 2.0, _dev(lam), u, M=16, period_L=info["side"])  # L too small
+        rbf.fmm_matvec(t, O.IMQ, 2.0, _dev(lam), u, M=16, period_L=1.5 * info["side"])  # L < 2 side with taper
     with pytest.raises(rbf.RbfError):
         rbf.fmm_matvec(t, O.IMQ, 2.0, _dev(lam), u, M=16, csample=0)  # closed form is Gaussian-only

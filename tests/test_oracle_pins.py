@@ -313,3 +313,22 @@ def test_direct_sum_small_cases():
     A = np.stack([O.direct(Y, e, O.IMQ, 2.0) for e in np.eye(60)], axis=1)
     assert np.allclose(A, A.T, atol=1e-15)
     assert np.max(np.linalg.eigvalsh(A)) <= 60 * 1.0
+
+
+# ----------------------------------------------------------- T-GMRES -----
+def test_oracle_gmres_matches_dense_solve():
+    """GMRES(m) with restarts reaches the dense LAPACK solution of a symmetric positive
+    definite RBF system (IMQ eps=50, 300 centres), and the iteration stops at the tolerance."""
+    from oracle.solver import gmres
+    rng = np.random.default_rng(12)
+    X = rng.random((300, 2))
+    r = np.linalg.norm(X[:, None, :] - X[None, :, :], axis=2)
+    A = O.phi(O.IMQ, 50.0, r)          # condition number ~3e3
+    b = rng.standard_normal(300)
+    x_ref = np.linalg.solve(A, b)
+    x, it, hist = gmres(lambda v: A @ v, b, m=20, tol=1e-12, maxit=5000)
+    assert np.linalg.norm(A @ x - b) <= 1e-12 * np.linalg.norm(b) * 1.01
+    assert np.linalg.norm(x - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+    assert len(hist) >= 2 and it > 20          # several restarts were exercised
+    # gamma_max <= N max|Phi| (Gershgorin, Sec. 3.1)
+    assert np.max(np.linalg.eigvalsh(A)) <= 300 * 1.0
