@@ -79,6 +79,8 @@ def load():
                                    _c_vp, _c_vp]
     lib.rbf_interp_solve.argtypes = [_c_vp, _c_int, _c_dbl, P(FmmParams), _c_vp, _c_vp, _c_int,
                                      P(SolveOpts), P(SolveReport), _c_vp]
+    lib.rbf_morton_order_noalloc.argtypes = [_c_vp, _c_i64, _c_int, _c_vp, _c_dbl, _c_int, _c_vp,
+                                             _c_vp, _c_vp]
     lib.rbf_profile.argtypes = [_c_vp, _c_int]
     lib.rbf_profile_read.argtypes = [_c_vp, _c_vp, _c_vp]
     lib.rbf_tree_free.argtypes = [_c_vp]
@@ -290,3 +292,17 @@ def interp_solve(tree: Tree, kernel: int, eps: float, u, lam, restart_m=50, max_
     if code not in (0, -4):
         raise RbfError(code, "rbf_interp_solve")
     return report
+
+
+def morton_order_noalloc(X, lo, side, depth, perm, keys):
+    """rbf_morton_order_noalloc: X (N, d) float64, perm (N,) int32 and keys (N,) uint64 or
+    int64 CUDA tensors (written).  Allocates no device memory."""
+    import torch
+    N, d = X.shape
+    lo_arr = (ctypes.c_double * d)(*[float(v) for v in np.asarray(lo).reshape(d)])
+    if perm.dtype != torch.int32 or keys.dtype not in (torch.int64, torch.uint64):
+        raise TypeError("morton_order_noalloc: perm must be int32 and keys 64-bit")
+    _check(load().rbf_morton_order_noalloc(_dev(X, "float64", "X"), N, d, lo_arr, float(side),
+                                           int(depth), ctypes.c_void_p(perm.data_ptr()),
+                                           ctypes.c_void_p(keys.data_ptr()), _stream()),
+           "rbf_morton_order_noalloc")

@@ -4,6 +4,7 @@
 // so that it is bit-exact with a plain sequential construction.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "rbf_internal.cuh"
@@ -711,4 +712,115 @@ extern "C" void rbf_tree_free(rbf_tree *t)
     }
     rbf_free(t->scratch);
     delete t;
+}
+
+// -------------------------------------------------- allocation-free ordering --
+// Morton keys and their stable radix sort with every temporary buffer in one
+// file-scope device arena instead of cudaMalloc'd memory.  This entry point has
+// no counterpart in the paper; it serves callers that must not allocate device
+// memory at call time (see include/rbf.h).
+namespace {
+
+constexpr int64_t NOALLOC_MAX_N = (int64_t)1 << 22;
+constexpr int64_t NOALLOC_MAX_BLK = (NOALLOC_MAX_N + RS_TILE - 1) / RS_TILE;
+constexpr int64_t NOALLOC_HIST = 256 * NOALLOC_MAX_BLK;
+constexpr int64_t NOALLOC_L1 = (NOALLOC_HIST + SCAN_TILE - 1) / SCAN_TILE;
+static_assert(NOALLOC_L1 <= SCAN_TILE, "two scan levels must cover the histogram");
+
+constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t OFF_LO = 0;
+constexpr size_t OFF_KEYS = OFF_LO + align256(RBF_MAX_DIM * sizeof(double));
+constexpr size_t OFF_VALS = OFF_KEYS + align256(NOALLOC_MAX_N * sizeof(uint64_t));
+constexpr size_t OFF_HIST = OFF_VALS + align256(NOALLOC_MAX_N * sizeof(int32_t));
+constexpr size_t OFF_OFFS = OFF_HIST + align256(NOALLOC_HIST * sizeof(int32_t));
+constexpr size_t OFF_BSUM = OFF_OFFS + align256(NOALLOC_HIST * sizeof(int32_t));
+constexpr size_t OFF_BOFF = OFF_BSUM + align256(NOALLOC_L1 * sizeof(int32_t));
+constexpr size_t ARENA_BYTES = OFF_BOFF + align256(NOALLOC_L1 * sizeof(int32_t));
+
+// The arena: every GPU that loads the library holds it until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_arena[ARENA_BYTES];
+
+std::mutex g_arena_mu;
+void *g_arena_dev[256] = {nullptr};
+
+// Device address of the arena on the current device, looked up once per device.
+int arena_address(unsigned char **out)
+{
+    int dev = 0;
+    RBF_CUDA_TRY(cudaGetDevice(&dev));
+    RBF_REQUIRE(dev >= 0 && dev < 256, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_arena_mu);
+    if (!g_arena_dev[dev]) {
+        void *p = nullptr;
+        RBF_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_arena));
+        g_arena_dev[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_arena_dev[dev]);
+    return RBF_OK;
+}
+
+// exclusive scan of n <= NOALLOC_HIST entries with two levels of block sums
+int scan_noalloc(const int32_t *in, int32_t *out, int64_t n, int32_t *bsum, int32_t *boff,
+                 cudaStream_t s)
+{
+    const int64_t nblk = (n + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_tile<<<(unsigned)nblk, SCAN_BS, 0, s>>>(in, out, n, bsum);
+    RBF_LAUNCH_CHECK();
+    if (nblk > 1) {
+        k_scan_tile<<<1, SCAN_BS, 0, s>>>(bsum, boff, nblk, nullptr);
+        RBF_LAUNCH_CHECK();
+        k_scan_add<<<ceil_div(n, 256), 256, 0, s>>>(out, n, boff);
+        RBF_LAUNCH_CHECK();
+    }
+    return RBF_OK;
+}
+
+}  // namespace
+
+extern "C" int rbf_morton_order_noalloc(const double *X, int64_t N, int d, const double *lo_host,
+                                        double side, int depth, int32_t *perm, uint64_t *keys,
+                                        void *stream)
+{
+    RBF_REQUIRE(X && lo_host && perm && keys, "rbf_morton_order_noalloc: NULL pointer");
+    RBF_REQUIRE(N >= 1 && N <= NOALLOC_MAX_N,
+                "rbf_morton_order_noalloc: N=%lld outside [1, %lld], the size of its fixed arena",
+                (long long)N, (long long)NOALLOC_MAX_N);
+    RBF_REQUIRE(d >= 1 && d <= RBF_MAX_DIM, "rbf_morton_order_noalloc: d=%d out of range", d);
+    RBF_REQUIRE(depth >= 0 && depth <= RBF_MAX_DEPTH && d * depth <= 63,
+                "rbf_morton_order_noalloc: depth=%d out of range for d=%d", depth, d);
+    RBF_REQUIRE(side > 0.0, "rbf_morton_order_noalloc: side must be > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char *arena = nullptr;
+    RBF_TRY(arena_address(&arena));
+    double *lo_d = reinterpret_cast<double *>(arena + OFF_LO);
+    uint64_t *kalt = reinterpret_cast<uint64_t *>(arena + OFF_KEYS);
+    int32_t *valt = reinterpret_cast<int32_t *>(arena + OFF_VALS);
+    int32_t *hist = reinterpret_cast<int32_t *>(arena + OFF_HIST);
+    int32_t *offs = reinterpret_cast<int32_t *>(arena + OFF_OFFS);
+    int32_t *bsum = reinterpret_cast<int32_t *>(arena + OFF_BSUM);
+    int32_t *boff = reinterpret_cast<int32_t *>(arena + OFF_BOFF);
+    // every arena region below is fully written before it is read
+    RBF_CUDA_TRY(cudaMemcpyAsync(lo_d, lo_host, d * sizeof(double), cudaMemcpyHostToDevice, s));
+    k_keys<<<ceil_div(N, 256), 256, 0, s>>>(X, N, d, depth, lo_d, side, keys, perm);
+    RBF_LAUNCH_CHECK();
+    const int nbits = d * depth;
+    const int nblk = (int)((N + RS_TILE - 1) / RS_TILE);
+    uint64_t *ka = keys, *kb = kalt;
+    int32_t *va = perm, *vb = valt;
+    if (N > 1) {
+        for (int shift = 0; shift < nbits; shift += 8) {
+            k_rs_hist<<<nblk, RS_BS, 0, s>>>(ka, N, shift, hist, nblk);
+            RBF_LAUNCH_CHECK();
+            RBF_TRY(scan_noalloc(hist, offs, (int64_t)256 * nblk, bsum, boff, s));
+            k_rs_scatter<<<nblk, RS_BS, 0, s>>>(ka, va, kb, vb, N, shift, offs, nblk);
+            RBF_LAUNCH_CHECK();
+            std::swap(ka, kb);
+            std::swap(va, vb);
+        }
+    }
+    if (ka != keys) {
+        RBF_CUDA_TRY(cudaMemcpyAsync(keys, ka, N * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        RBF_CUDA_TRY(cudaMemcpyAsync(perm, va, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    }
+    return RBF_OK;
 }
