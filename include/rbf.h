@@ -257,6 +257,90 @@ RBF_API int rbf_morton_order_noalloc(const double *X, int64_t N, int d, const do
                                      double side, int depth, int32_t *perm, uint64_t *keys,
                                      void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned approximate-cardinal preconditioner for rbf_interp_solve.
+ * Column i of P carries weights on the RBF_KNN nearest centres S_i of centre i
+ * (itself first), approximating its local cardinal function: sum_{j in S_i}
+ * w_j Phi(x_k - x_j) = delta_{ik} on S_i.  A small MLP maps eps-scaled
+ * neighbour offsets to the direction of those weights; each column is then
+ * scaled so that it is exactly cardinal at its own centre.  The network is
+ * trained on exact FP64 local solves.  The paper has no preconditioner: this
+ * is an extension of its Krylov solve (Sec. 1).
+ * ------------------------------------------------------------------------- */
+#define RBF_KNN 32
+
+/* k-nearest neighbours of every centre (RBF_KNN of them, itself included),
+ * ascending squared distance sum_t (x_t - y_t)^2 in FP64, ties by original
+ * index.  idx_host: host int64[N][RBF_KNN], original indices.  Computed on
+ * the device once per tree (rings of leaves until the k-th distance is
+ * certified) and kept.  Synchronises `stream`. */
+RBF_API int rbf_knn(rbf_tree *t, int64_t *idx_host, void *stream);
+
+/* Exact local cardinal coefficients c = (A_S + delta I)^-1 e_1 on S = the
+ * neighbours of each listed centre (original indices centres_host[nc]), with
+ * A_S[j][k] = Phi(x_j - x_k) and delta = delta_rel * ||A_S||_F; FP64 Cholesky,
+ * one warp per centre.  A failed factorisation yields NaN.  c_host: host
+ * double[nc][RBF_KNN].  Synchronises `stream`. */
+RBF_API int rbf_cardinal_weights(rbf_tree *t, rbf_kernel kernel, double eps, double delta_rel,
+                                 const int64_t *centres_host, int64_t nc, double *c_host,
+                                 void *stream);
+
+/* Network input of each listed centre: eps (x_j - x_i) for its neighbours j in
+ * distance order, flattened (RBF_KNN * d floats).  F: device float[nc][32 d]. */
+RBF_API int rbf_precond_features(rbf_tree *t, double eps, const int64_t *centres_host, int64_t nc,
+                                 float *F, void *stream);
+
+/* The network: d_in -> width -> width -> width -> d_out, ReLU on the hidden
+ * layers, FP32 master weights with BF16 copies for the tensor-core GEMMs
+ * (mma.sync BF16, FP32 accumulation).  Parameters are flattened layer by layer
+ * as W_l (out x in, row-major) then b_l.  Initial weights: He-normal from a
+ * counter-based generator (SplitMix64 + Box-Muller) seeded by `seed`, zero
+ * biases. */
+typedef struct rbf_mlp rbf_mlp;
+RBF_API int rbf_mlp_create(int d_in, int width, int d_out, uint64_t seed, rbf_mlp **out);
+RBF_API int rbf_mlp_num_params(const rbf_mlp *net, int64_t *count);
+RBF_API int rbf_mlp_get_params(const rbf_mlp *net, float *host);
+/* Sets the FP32 master weights (and their BF16 copies) and resets Adam. */
+RBF_API int rbf_mlp_set_params(rbf_mlp *net, const float *host);
+/* Y[B][d_out] = network(X[B][d_in]); device FP32 arrays. */
+RBF_API int rbf_mlp_forward(rbf_mlp *net, const float *X, int64_t B, float *Y, void *stream);
+/* Gradient of mean((Y - T)^2) with respect to the flattened parameters into
+ * grad (device float[num_params]); *loss_host (may be NULL) gets the loss. */
+RBF_API int rbf_mlp_gradient(rbf_mlp *net, const float *X, const float *T, int64_t B, float *grad,
+                             float *loss_host, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on that loss. */
+RBF_API int rbf_mlp_train_step(rbf_mlp *net, const float *X, const float *T, int64_t B, float lr,
+                               float *loss_host, void *stream);
+RBF_API void rbf_mlp_free(rbf_mlp *net);
+
+typedef struct {
+    int n_train;      /* training centres, evenly spaced in Morton order */
+    int epochs;
+    int batch;
+    float lr;         /* Adam step size */
+    double delta_rel; /* regularisation of the local solves */
+} rbf_train_opts;
+
+typedef struct {
+    float loss_first, loss_last; /* first and last mini-batch loss */
+    int steps;
+    double seconds;
+} rbf_train_report;
+
+/* Train `net` (shape 32 d -> 32) on this tree's centres: exact local cardinal
+ * solves give targets c / max|c|; every step runs on the device.  Synchronises. */
+RBF_API int rbf_precond_train(rbf_tree *t, rbf_kernel kernel, double eps, rbf_mlp *net,
+                              const rbf_train_opts *opts, rbf_train_report *rep_host, void *stream);
+
+/* Build P for this tree from the network (net != NULL) or from exact local
+ * solves (net == NULL), then attach it: rbf_interp_solve uses it when
+ * opts.precond == 1.  Synchronises. */
+RBF_API int rbf_precond_build(rbf_tree *t, rbf_kernel kernel, double eps, rbf_mlp *net,
+                              double delta_rel, void *stream);
+
+/* z = P y (device FP64 vectors in the caller's order).  Synchronises. */
+RBF_API int rbf_precond_apply(rbf_tree *t, const double *y, double *z, void *stream);
+
 /* Release a tree and everything it owns.  NULL is accepted. */
 RBF_API void rbf_tree_free(rbf_tree *t);
 

@@ -46,6 +46,16 @@ class SolveReport(ctypes.Structure):
                 ("matvecs_fp64", _c_int)]
 
 
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("n_train", _c_int), ("epochs", _c_int), ("batch", _c_int), ("lr", ctypes.c_float),
+                ("delta_rel", _c_dbl)]
+
+
+class TrainReport(ctypes.Structure):
+    _fields_ = [("loss_first", ctypes.c_float), ("loss_last", ctypes.c_float), ("steps", _c_int),
+                ("seconds", _c_dbl)]
+
+
 class RbfError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -81,6 +91,23 @@ def load():
                                      P(SolveOpts), P(SolveReport), _c_vp]
     lib.rbf_morton_order_noalloc.argtypes = [_c_vp, _c_i64, _c_int, _c_vp, _c_dbl, _c_int, _c_vp,
                                              _c_vp, _c_vp]
+    lib.rbf_knn.argtypes = [_c_vp, _c_vp, _c_vp]
+    lib.rbf_cardinal_weights.argtypes = [_c_vp, _c_int, _c_dbl, _c_dbl, _c_vp, _c_i64, _c_vp, _c_vp]
+    lib.rbf_precond_features.argtypes = [_c_vp, _c_dbl, _c_vp, _c_i64, _c_vp, _c_vp]
+    lib.rbf_mlp_create.argtypes = [_c_int, _c_int, _c_int, ctypes.c_uint64, P(_c_vp)]
+    lib.rbf_mlp_num_params.argtypes = [_c_vp, P(_c_i64)]
+    lib.rbf_mlp_get_params.argtypes = [_c_vp, _c_vp]
+    lib.rbf_mlp_set_params.argtypes = [_c_vp, _c_vp]
+    lib.rbf_mlp_forward.argtypes = [_c_vp, _c_vp, _c_i64, _c_vp, _c_vp]
+    lib.rbf_mlp_gradient.argtypes = [_c_vp, _c_vp, _c_vp, _c_i64, _c_vp, P(ctypes.c_float), _c_vp]
+    lib.rbf_mlp_train_step.argtypes = [_c_vp, _c_vp, _c_vp, _c_i64, ctypes.c_float,
+                                       P(ctypes.c_float), _c_vp]
+    lib.rbf_mlp_free.argtypes = [_c_vp]
+    lib.rbf_mlp_free.restype = None
+    lib.rbf_precond_train.argtypes = [_c_vp, _c_int, _c_dbl, _c_vp, P(TrainOpts), P(TrainReport),
+                                      _c_vp]
+    lib.rbf_precond_build.argtypes = [_c_vp, _c_int, _c_dbl, _c_vp, _c_dbl, _c_vp]
+    lib.rbf_precond_apply.argtypes = [_c_vp, _c_vp, _c_vp, _c_vp]
     lib.rbf_profile.argtypes = [_c_vp, _c_int]
     lib.rbf_profile_read.argtypes = [_c_vp, _c_vp, _c_vp]
     lib.rbf_tree_free.argtypes = [_c_vp]
@@ -306,3 +333,116 @@ def morton_order_noalloc(X, lo, side, depth, perm, keys):
                                            int(depth), ctypes.c_void_p(perm.data_ptr()),
                                            ctypes.c_void_p(keys.data_ptr()), _stream()),
            "rbf_morton_order_noalloc")
+
+
+KNN = 32
+
+
+def _np_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def knn(tree: Tree) -> np.ndarray:
+    """rbf_knn: (N, 32) int64 original indices of the nearest centres, nearest first."""
+    N = tree.info()["N"]
+    out = np.empty((N, KNN), dtype=np.int64)
+    _check(load().rbf_knn(tree.handle, _np_ptr(out), _stream()), "rbf_knn")
+    return out
+
+
+def cardinal_weights(tree: Tree, kernel: int, eps: float, delta_rel: float, centres) -> np.ndarray:
+    """rbf_cardinal_weights: (nc, 32) FP64 local cardinal coefficients."""
+    c = np.ascontiguousarray(centres, dtype=np.int64)
+    out = np.empty((len(c), KNN), dtype=np.float64)
+    _check(load().rbf_cardinal_weights(tree.handle, kernel, float(eps), float(delta_rel), _np_ptr(c),
+                                       len(c), _np_ptr(out), _stream()), "rbf_cardinal_weights")
+    return out
+
+
+def precond_features(tree: Tree, eps: float, centres, F):
+    """rbf_precond_features into the float32 CUDA tensor F of shape (nc, 32 d)."""
+    c = np.ascontiguousarray(centres, dtype=np.int64)
+    _check(load().rbf_precond_features(tree.handle, float(eps), _np_ptr(c), len(c),
+                                       _dev(F, "float32", "F"), _stream()), "rbf_precond_features")
+    return F
+
+
+class Mlp:
+    """Owner of an rbf_mlp handle."""
+
+    def __init__(self, d_in, width, d_out, seed=0):
+        h = ctypes.c_void_p()
+        _check(load().rbf_mlp_create(d_in, width, d_out, seed, ctypes.byref(h)), "rbf_mlp_create")
+        self._h = h
+        self.d_in, self.width, self.d_out = d_in, width, d_out
+
+    @property
+    def handle(self):
+        return self._h
+
+    def num_params(self) -> int:
+        n = _c_i64(0)
+        _check(load().rbf_mlp_num_params(self._h, ctypes.byref(n)), "rbf_mlp_num_params")
+        return n.value
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params(), dtype=np.float32)
+        _check(load().rbf_mlp_get_params(self._h, _np_ptr(out)), "rbf_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load().rbf_mlp_set_params(self._h, _np_ptr(p)), "rbf_mlp_set_params")
+
+    def forward(self, X, Y):
+        _check(load().rbf_mlp_forward(self._h, _dev(X, "float32", "X"), X.shape[0],
+                                      _dev(Y, "float32", "Y"), _stream()), "rbf_mlp_forward")
+        return Y
+
+    def gradient(self, X, T, G):
+        loss = ctypes.c_float(0)
+        _check(load().rbf_mlp_gradient(self._h, _dev(X, "float32", "X"), _dev(T, "float32", "T"),
+                                       X.shape[0], _dev(G, "float32", "G"), ctypes.byref(loss),
+                                       _stream()), "rbf_mlp_gradient")
+        return loss.value
+
+    def train_step(self, X, T, lr):
+        loss = ctypes.c_float(0)
+        _check(load().rbf_mlp_train_step(self._h, _dev(X, "float32", "X"), _dev(T, "float32", "T"),
+                                         X.shape[0], float(lr), ctypes.byref(loss), _stream()),
+               "rbf_mlp_train_step")
+        return loss.value
+
+    def free(self):
+        if self._h:
+            load().rbf_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def precond_train(tree: Tree, kernel: int, eps: float, net: Mlp, n_train=8192, epochs=200,
+                  batch=1024, lr=1e-3, delta_rel=1e-12) -> dict:
+    o = TrainOpts(n_train, epochs, batch, lr, delta_rel)
+    r = TrainReport()
+    _check(load().rbf_precond_train(tree.handle, kernel, float(eps), net.handle, ctypes.byref(o),
+                                    ctypes.byref(r), _stream()), "rbf_precond_train")
+    return {"loss_first": r.loss_first, "loss_last": r.loss_last, "steps": r.steps,
+            "seconds": r.seconds}
+
+
+def precond_build(tree: Tree, kernel: int, eps: float, net=None, delta_rel=1e-12):
+    """rbf_precond_build from the network (net) or exact local solves (net=None)."""
+    _check(load().rbf_precond_build(tree.handle, kernel, float(eps),
+                                    net.handle if net is not None else None, float(delta_rel),
+                                    _stream()), "rbf_precond_build")
+
+
+def precond_apply(tree: Tree, y, z):
+    _check(load().rbf_precond_apply(tree.handle, _dev(y, "float64", "y"), _dev(z, "float64", "z"),
+                                    _stream()), "rbf_precond_apply")
+    return z

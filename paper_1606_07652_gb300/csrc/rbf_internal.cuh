@@ -114,6 +114,17 @@ struct rbf_prof {
     int64_t launches[RBF_PASS_COUNT] = {0};
 };
 
+// learned / exact approximate-cardinal preconditioner P (sorted order)
+struct rbf_precond_data {
+    int32_t *nbr = nullptr;      // [N][RBF_KNN] sorted ids of the nearest centres, nearest first
+    double *W = nullptr;         // [N][RBF_KNN] weights of column i on nbr[i][k]
+    int32_t *row_off = nullptr;  // [N+1] rows of P: entries row_off[j] .. row_off[j+1]-1
+    int32_t *ent = nullptr;      // [N*RBF_KNN] entry ids (i*RBF_KNN + k) by row, columns ascending
+    bool ready = false;
+    int kernel = -1;
+    double eps = 0.0;
+};
+
 struct rbf_tree {
     int64_t N = 0;
     int d = 0, D = 0;
@@ -134,6 +145,7 @@ struct rbf_tree {
     rbf_level lev[RBF_MAX_DEPTH + 1];
     rbf_plan *plan[2] = {nullptr, nullptr};  // indexed by rbf_precision
     rbf_prof prof;
+    rbf_precond_data pc;
     // generic device scratch for solver/host-API copies
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -156,6 +168,8 @@ int rbf_scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *
                            cudaStream_t s);
 int rbf_build_il(rbf_tree *t, int level, cudaStream_t s);
 void rbf_prof_release(rbf_tree *t);
+void rbf_precond_release(rbf_tree *t);
+int rbf_precond_apply_sorted(const rbf_tree *t, const double *y, double *z, cudaStream_t s);
 
 // --------------------------------------------------------------- plan -----
 // Half-spectrum layout of an expansion: dimension 0 keeps k0 = 0..M/2,

@@ -117,6 +117,7 @@ struct Solver {
     double *w = nullptr, *z = nullptr, *r = nullptr, *part = nullptr, *hd = nullptr;
     std::vector<double> hh;  // host copy of reductions
     int mv_inner = 0, mv64 = 0;
+    bool use_p = false;      // right preconditioner P attached to the tree
 
     int alloc(int m_)
     {
@@ -165,8 +166,13 @@ struct Solver {
         else ++mv_inner;
         return rbf_matvec_sorted64(t, kernel, eps, params, prec, x, y, s);
     }
-    // A (P x): right preconditioning; P = identity here
-    int apply_op(int prec, const double *x, double *y) { return matvec(prec, x, y); }
+    // A (P x): right preconditioning (P = identity unless use_p)
+    int apply_op(int prec, const double *x, double *y)
+    {
+        if (!use_p) return matvec(prec, x, y);
+        RBF_TRY(rbf_precond_apply_sorted(t, x, z, s));
+        return matvec(prec, z, y);
+    }
 
     // GMRES(m) on A x = b, x in/out, stops when ||b - A x|| <= tol_abs (estimate).
     int gmres(int prec, const double *b, double *x, bool x_zero, double tol_abs, int maxit,
@@ -271,8 +277,9 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
     RBF_REQUIRE(opts->max_iters >= 1 && opts->max_refine >= 1, "iteration limits must be >= 1");
     RBF_REQUIRE(opts->rtol > 0.0, "rtol must be > 0");
     RBF_REQUIRE(opts->inner_prec == RBF_FP64 || opts->inner_prec == RBF_FP32, "inner_prec");
-    RBF_REQUIRE(opts->precond == 0, "precond=%d: no preconditioner is attached to this tree",
-                opts->precond);
+    RBF_REQUIRE(opts->precond == 0 || opts->precond == 1, "precond=%d", opts->precond);
+    RBF_REQUIRE(opts->precond == 0 || t->pc.ready,
+                "precond=1: no preconditioner is attached to this tree (rbf_precond_build)");
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = t->N;
@@ -284,7 +291,9 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
     sv.s = s;
     sv.n = n;
     int st = sv.alloc(opts->restart_m);
-    double *us = nullptr, *ls = nullptr, *ax = nullptr, *dl = nullptr;
+    double *us = nullptr, *ls = nullptr, *ax = nullptr, *dl = nullptr, *lprev = nullptr;
+    int fallback = 0;
+    if (st == RBF_OK) st = rbf_alloc(&lprev, n);
     if (st == RBF_OK) st = rbf_alloc(&us, n);
     if (st == RBF_OK) st = rbf_alloc(&ls, n);
     if (st == RBF_OK) st = rbf_alloc(&ax, n);
@@ -302,9 +311,11 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
         if (st != RBF_OK) break;
         if (nu == 0.0) nu = 1.0;
         double rel = INFINITY, prev = INFINITY;
-        int it_c = 0;
+        int it_c = 0, k = 0;
         bool conv = false;
-        for (int k = 0; k < opts->max_refine; ++k) {
+        sv.use_p = opts->precond == 1;
+        bool last_used_p = false;
+        while (k < opts->max_refine) {
             // true residual with the FP64 product
             if ((st = sv.matvec(RBF_FP64, ls, ax)) != RBF_OK) break;
             k_sub<<<gb, bs, 0, s>>>(us, ax, sv.r, n);
@@ -315,11 +326,24 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
                 conv = true;
                 break;
             }
-            if (!std::isfinite(rel) || (k > 0 && rel > 0.5 * prev)) break;  // stagnation
+            const bool stalled = !std::isfinite(rel) || (k > 0 && rel > 0.5 * prev);
+            if (stalled && last_used_p) {
+                // the preconditioned step did not pay off on the FP64 residual: undo it
+                // and continue with the plain (identity-preconditioned) iteration
+                RBF_CUDA_TRY(cudaMemcpyAsync(ls, lprev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                sv.use_p = false;
+                last_used_p = false;
+                fallback = 1;
+                prev = INFINITY;  // the restored iterate starts a fresh progress test
+                continue;
+            }
+            if (stalled) break;
             prev = rel;
             if (it_c >= opts->max_iters) break;
             ++refinements;
-            // inner solve A delta = r
+            ++k;
+            RBF_CUDA_TRY(cudaMemcpyAsync(lprev, ls, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            // inner solve A P y = r, delta = P y
             const double floor_inner = opts->inner_prec == RBF_FP32 ? 2e-6 : 0.0;
             const double eta = std::max(0.5 * opts->rtol / rel, floor_inner);
             RBF_CUDA_TRY(cudaMemsetAsync(dl, 0, n * sizeof(double), s));
@@ -330,7 +354,13 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
             st = sv.gmres(opts->inner_prec, rr, dl, true, eta * rn, opts->max_iters - it_c, &its, &est);
             if (st != RBF_OK) break;
             it_c += its;
-            k_axpy<<<gb, bs, 0, s>>>(1.0, dl, ls, n);
+            last_used_p = sv.use_p;
+            if (sv.use_p) {
+                if ((st = rbf_precond_apply_sorted(t, dl, sv.w, s)) != RBF_OK) break;
+                k_axpy<<<gb, bs, 0, s>>>(1.0, sv.w, ls, n);
+            } else {
+                k_axpy<<<gb, bs, 0, s>>>(1.0, dl, ls, n);
+            }
         }
         if (st != RBF_OK) break;
         total_it += it_c;
@@ -350,10 +380,11 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
     rbf_free(ls);
     rbf_free(ax);
     rbf_free(dl);
+    rbf_free(lprev);
     if (rep) {
         rep->iters = total_it;
         rep->refinements = refinements;
-        rep->used_fallback = 0;
+        rep->used_fallback = fallback;
         rep->rel_resid = worst;
         rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         rep->matvecs_inner = sv.mv_inner;

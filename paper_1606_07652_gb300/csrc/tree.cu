@@ -398,7 +398,7 @@ int rbf_scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *
     return RBF_OK;
 }
 
-static int radix_sort(uint64_t *keys, int32_t *vals, int64_t n, int nbits, cudaStream_t s)
+int rbf_radix_sort_pairs(uint64_t *keys, int32_t *vals, int64_t n, int nbits, cudaStream_t s)
 {
     if (nbits <= 0 || n <= 1) return RBF_OK;
     int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
@@ -469,7 +469,7 @@ static int build_impl(rbf_tree *t, const double *X, cudaStream_t s)
     RBF_TRY(rbf_alloc(&t->perm, N));
     k_keys<<<ceil_div(N, 256), 256, 0, s>>>(X, N, d, D, lo_d, t->side, t->keys, t->perm);
     RBF_LAUNCH_CHECK();
-    RBF_TRY(radix_sort(t->keys, t->perm, N, d * D, s));
+    RBF_TRY(rbf_radix_sort_pairs(t->keys, t->perm, N, d * D, s));
     rbf_free(lo_d);
 
     RBF_TRY(rbf_alloc(&t->xs64, (size_t)N * d));
@@ -693,6 +693,7 @@ extern "C" void rbf_tree_free(rbf_tree *t)
 {
     if (!t) return;
     rbf_prof_release(t);
+    rbf_precond_release(t);
     rbf_plan_free(t->plan[0]);
     rbf_plan_free(t->plan[1]);
     rbf_free(t->keys);

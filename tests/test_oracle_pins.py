@@ -332,3 +332,65 @@ def test_oracle_gmres_matches_dense_solve():
     assert len(hist) >= 2 and it > 20          # several restarts were exercised
     # gamma_max <= N max|Phi| (Gershgorin, Sec. 3.1)
     assert np.max(np.linalg.eigvalsh(A)) <= 300 * 1.0
+
+
+# ---------------------------------------------- learned preconditioner ----
+def test_oracle_mlp_gradient_matches_finite_differences():
+    """T-MLP-FD: the oracle's backward pass equals central differences of the loss."""
+    from oracle.solver import mlp_init, mlp_forward, mlp_backward, mse_loss
+    rng = np.random.default_rng(6)
+    W, b = mlp_init([12, 16, 16, 16, 5], seed=1)
+    for bl in b:
+        bl += 0.1 * rng.standard_normal(bl.shape)   # move biases off zero (ReLU kinks)
+    X = rng.standard_normal((7, 12))
+    T = rng.standard_normal((7, 5))
+    Y, cache = mlp_forward(W, b, X)
+    gW, gb = mlp_backward(W, b, cache, Y, T)
+    h = 1e-6
+    for l in range(4):
+        for (i, j) in [(0, 0), (W[l].shape[0] - 1, W[l].shape[1] - 1), (1, 2)]:
+            W[l][i, j] += h
+            lp = mse_loss(mlp_forward(W, b, X)[0], T)
+            W[l][i, j] -= 2 * h
+            lm = mse_loss(mlp_forward(W, b, X)[0], T)
+            W[l][i, j] += h
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - gW[l][i, j]) <= 1e-6 * max(1e-3, abs(fd))
+        b[l][0] += h
+        lp = mse_loss(mlp_forward(W, b, X)[0], T)
+        b[l][0] -= 2 * h
+        lm = mse_loss(mlp_forward(W, b, X)[0], T)
+        b[l][0] += h
+        assert abs((lp - lm) / (2 * h) - gb[l][0]) <= 1e-6 * max(1e-3, abs(gb[l][0]))
+
+
+def test_oracle_cardinal_coefficients_are_cardinal():
+    """T-CARD: sum_{j in S} c_j Phi(x_k - x_j) = delta_{k, centre} for k in S."""
+    from oracle.solver import knn, cardinal
+    rng = np.random.default_rng(8)
+    X = rng.random((400, 2))
+    nb = knn(X, 32)
+    c = cardinal(X, nb[:50], O.GAUSSIAN, 40.0, 0.0)   # eps*h ~ 2: well-conditioned local sets
+    for i in range(50):
+        P = X[nb[i]]
+        A = O.phi(O.GAUSSIAN, 40.0, np.linalg.norm(P[:, None] - P[None, :], axis=2))
+        e = np.zeros(32)
+        e[0] = 1.0
+        assert np.max(np.abs(A @ c[i] - e)) < 1e-10
+
+
+def test_oracle_knn_by_hand():
+    """Neighbour order with an exact distance tie broken by index."""
+    from oracle.solver import knn
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [-1.0, 0.0], [0.0, 0.5], [3.0, 3.0]])
+    nb = knn(X, 4)
+    assert nb[0].tolist() == [0, 3, 1, 2]      # 1 and 2 tie at distance 1
+    assert nb[4].tolist()[0] == 4
+
+
+def test_bf16_rounding_by_hand():
+    """BF16 keeps 8 significant bits, ties to even: 1 + 2^-8 (a tie) -> 1; 1 + 3*2^-8 -> 1 + 2^-6;
+    1 + 2^-7 is representable."""
+    from oracle.solver import bf16_round
+    v = bf16_round(np.array([1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -7, -2.5]))
+    assert v.tolist() == [1.0, 1.0 + 2 ** -6, 1.0 + 2 ** -7, -2.5]
