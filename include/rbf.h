@@ -341,6 +341,69 @@ RBF_API int rbf_precond_build(rbf_tree *t, rbf_kernel kernel, double eps, rbf_ml
 /* z = P y (device FP64 vectors in the caller's order).  Synchronises. */
 RBF_API int rbf_precond_apply(rbf_tree *t, const double *y, double *z, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Autotuning and batches of independent problems.
+ * ------------------------------------------------------------------------- */
+
+/* Largest |K(r) - Phi(r)| over 1024 sampled far offsets (w_D <= |r|_inf <= side,
+ * w_D = side / 2^depth) for the given expansion parameters; K is the far
+ * kernel of Eq. (35) built exactly as rbf_fmm_matvec builds it (FP64).  This
+ * is the per-pair error that the scaled Lemma, Eq. (33), multiplies by
+ * sum |lambda_j|.  Synchronises the device. */
+RBF_API int rbf_kernel_error(rbf_kernel kernel, double eps, int d, const rbf_fmm_params *params,
+                             double side, int depth, double *max_err_host);
+
+/* Pick the tree depth (about 32 points per leaf for d >= 3, 64 for d <= 2,
+ * depth >= 2), the period and taper (Gaussian: Phi(L - side) < tol / 100;
+ * inverse multiquadric: L = 4 side, alpha = 4.5) and the smallest even
+ * M in [8, 64] whose measured far-kernel error (rbf_kernel_error) is <= tol
+ * (64 when none is).  *err_out (may be NULL) receives the achieved error. */
+RBF_API int rbf_autotune(rbf_kernel kernel, double eps, int d, int64_t N, double side, double tol,
+                         rbf_fmm_params *params_out, int *depth_out, double *err_out);
+
+/* One problem of a batch: centres X (device [N][d] FP64, in [0,1]^d), kernel,
+ * shape parameter, and the number of right-hand sides. */
+typedef struct {
+    const double *X;
+    int64_t N;
+    int d;
+    rbf_kernel kernel;
+    double eps;
+    int nrhs;
+} rbf_problem;
+
+typedef struct rbf_batch rbf_batch;
+
+/* Autotune (tol_kernel) and build a tree for every problem (root [0,1]^d).
+ * Vectors of a batch are packed: problem p's right-hand side r occupies
+ * [off[p] + r N_p, off[p] + (r+1) N_p) of a device array of `total` doubles
+ * (rbf_batch_layout).  The problem array may be freed after the call; the
+ * centres must stay alive. */
+RBF_API int rbf_batch_create(const rbf_problem *problems_host, int n_problems, double tol_kernel,
+                             void *stream, rbf_batch **out);
+/* Host arrays of n_problems entries (any may be NULL). */
+RBF_API int rbf_batch_layout(const rbf_batch *b, int64_t *off_host, int *depth_host, int *M_host,
+                             int64_t *total_host);
+/* u = A lambda for every problem and right-hand side (packed device arrays).
+ * The first call per precision runs the products once (allocating plans) and
+ * captures them into one CUDA graph over several streams; every later call is
+ * a copy into the batch's own buffer, one graph launch and a copy out.
+ * Asynchronous after the first call. */
+RBF_API int rbf_batch_matvec(rbf_batch *b, rbf_precision prec, const double *lambda_packed,
+                             double *u_packed, void *stream);
+/* Restarted GMRES(m) on every system (problem, right-hand side) in lockstep:
+ * one graph launch of all products per step, batched CGS2 reductions on the
+ * device, Hessenberg problems on the host.  u_packed, lambda_packed: device
+ * arrays laid out like the batch buffers (lambda holds the initial guess).
+ * rel_resid_host[n_systems] (may be NULL) gets ||u - A lambda|| / ||u|| per
+ * system for the product in `prec`; *step_ms_host the mean wall time of a
+ * GMRES step.  No iterative refinement in batch mode.  Synchronises. */
+RBF_API int rbf_batch_solve(rbf_batch *b, const double *u_packed, double *lambda_packed,
+                            int restart_m, int max_iters, double rtol, rbf_precision prec,
+                            double *rel_resid_host, int *iters_host, double *step_ms_host,
+                            void *stream);
+RBF_API void rbf_batch_free(rbf_batch *b);
+
 /* Release a tree and everything it owns.  NULL is accepted. */
 RBF_API void rbf_tree_free(rbf_tree *t);
 

@@ -46,6 +46,11 @@ class SolveReport(ctypes.Structure):
                 ("matvecs_fp64", _c_int)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("X", _c_vp), ("N", _c_i64), ("d", _c_int), ("kernel", _c_int), ("eps", _c_dbl),
+                ("nrhs", _c_int)]
+
+
 class TrainOpts(ctypes.Structure):
     _fields_ = [("n_train", _c_int), ("epochs", _c_int), ("batch", _c_int), ("lr", ctypes.c_float),
                 ("delta_rel", _c_dbl)]
@@ -108,6 +113,17 @@ def load():
                                       _c_vp]
     lib.rbf_precond_build.argtypes = [_c_vp, _c_int, _c_dbl, _c_vp, _c_dbl, _c_vp]
     lib.rbf_precond_apply.argtypes = [_c_vp, _c_vp, _c_vp, _c_vp]
+    lib.rbf_kernel_error.argtypes = [_c_int, _c_dbl, _c_int, P(FmmParams), _c_dbl, _c_int,
+                                     P(_c_dbl)]
+    lib.rbf_autotune.argtypes = [_c_int, _c_dbl, _c_int, _c_i64, _c_dbl, _c_dbl, P(FmmParams),
+                                 P(_c_int), P(_c_dbl)]
+    lib.rbf_batch_create.argtypes = [_c_vp, _c_int, _c_dbl, _c_vp, P(_c_vp)]
+    lib.rbf_batch_layout.argtypes = [_c_vp, _c_vp, _c_vp, _c_vp, P(_c_i64)]
+    lib.rbf_batch_matvec.argtypes = [_c_vp, _c_int, _c_vp, _c_vp, _c_vp]
+    lib.rbf_batch_solve.argtypes = [_c_vp, _c_vp, _c_vp, _c_int, _c_int, _c_dbl, _c_int, _c_vp,
+                                    P(_c_int), P(_c_dbl), _c_vp]
+    lib.rbf_batch_free.argtypes = [_c_vp]
+    lib.rbf_batch_free.restype = None
     lib.rbf_profile.argtypes = [_c_vp, _c_int]
     lib.rbf_profile_read.argtypes = [_c_vp, _c_vp, _c_vp]
     lib.rbf_tree_free.argtypes = [_c_vp]
@@ -446,3 +462,79 @@ def precond_apply(tree: Tree, y, z):
     _check(load().rbf_precond_apply(tree.handle, _dev(y, "float64", "y"), _dev(z, "float64", "z"),
                                     _stream()), "rbf_precond_apply")
     return z
+
+
+def kernel_error(kernel, eps, d, M, period_L, window_alpha, side=1.0, depth=2) -> float:
+    """rbf_kernel_error: max |K - Phi| over sampled far offsets."""
+    p = FmmParams(M, period_L, window_alpha, 1)
+    e = _c_dbl(0)
+    _check(load().rbf_kernel_error(kernel, float(eps), d, ctypes.byref(p), float(side), depth,
+                                   ctypes.byref(e)), "rbf_kernel_error")
+    return e.value
+
+
+def autotune(kernel, eps, d, N, tol, side=1.0) -> dict:
+    p = FmmParams()
+    D = _c_int(0)
+    e = _c_dbl(0)
+    _check(load().rbf_autotune(kernel, float(eps), d, int(N), float(side), float(tol),
+                               ctypes.byref(p), ctypes.byref(D), ctypes.byref(e)), "rbf_autotune")
+    return {"M": p.M, "period_L": p.period_L, "window_alpha": p.window_alpha, "depth": D.value,
+            "err": e.value}
+
+
+class Batch:
+    """Owner of an rbf_batch: problems = list of dicts(X=CUDA float64 tensor (N, d), kernel,
+    eps, nrhs).  The tensors must outlive the batch."""
+
+    def __init__(self, problems, tol_kernel=1e-6):
+        arr = (Problem * len(problems))()
+        self._keep = []
+        for i, q in enumerate(problems):
+            X = q["X"]
+            self._keep.append(X)
+            arr[i] = Problem(_dev(X, "float64", "X"), X.shape[0], X.shape[1], q["kernel"],
+                             float(q["eps"]), int(q.get("nrhs", 1)))
+        h = ctypes.c_void_p()
+        _check(load().rbf_batch_create(arr, len(problems), float(tol_kernel), _stream(),
+                                       ctypes.byref(h)), "rbf_batch_create")
+        self._h = h
+        self.n = len(problems)
+        self.problems = problems
+
+    def layout(self):
+        off = np.empty(self.n, np.int64)
+        dep = np.empty(self.n, np.int32)
+        Ms = np.empty(self.n, np.int32)
+        tot = _c_i64(0)
+        _check(load().rbf_batch_layout(self._h, _np_ptr(off), _np_ptr(dep), _np_ptr(Ms),
+                                       ctypes.byref(tot)), "rbf_batch_layout")
+        return {"off": off, "depth": dep, "M": Ms, "total": tot.value}
+
+    def matvec(self, lam, u, prec=FP32):
+        """rbf_batch_matvec on packed float64 CUDA tensors of layout()["total"] entries."""
+        _check(load().rbf_batch_matvec(self._h, prec, _dev(lam, "float64", "lam"),
+                                       _dev(u, "float64", "u"), _stream()), "rbf_batch_matvec")
+        return u
+
+    def solve(self, u, lam, restart_m=30, max_iters=100, rtol=1e-6, prec=FP32):
+        nsys = sum(int(q.get("nrhs", 1)) for q in self.problems)
+        rr = np.empty(nsys, np.float64)
+        it = _c_int(0)
+        ms = _c_dbl(0)
+        _check(load().rbf_batch_solve(self._h, _dev(u, "float64", "u"), _dev(lam, "float64", "lam"),
+                                      restart_m, max_iters, float(rtol), prec, _np_ptr(rr),
+                                      ctypes.byref(it), ctypes.byref(ms), _stream()),
+               "rbf_batch_solve")
+        return {"rel_resid": rr, "iters": it.value, "step_ms": ms.value}
+
+    def free(self):
+        if self._h:
+            load().rbf_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
