@@ -168,7 +168,8 @@ RBF_API int rbf_direct_sum(const double *X, int64_t N, int d, rbf_kernel kernel,
 
 /* Solver options for rbf_interp_solve (Sec. 1: GMRES with the FMM product).
  *  restart_m   Krylov dimension per restart (1..200).
- *  max_iters   total inner iterations over all restarts and refinements.
+ *  max_iters   total inner iterations over all restarts and refinements; each
+ *              refinement step may use max(restart_m, max_iters / max_refine).
  *  max_refine  outer FP64 refinement steps (>= 1).
  *  rtol        target ||u - A lambda||_2 / ||u||_2, measured with the FP64 FMM.
  *  inner_prec  arithmetic of the matvec inside GMRES (RBF_FP64 or RBF_FP32).

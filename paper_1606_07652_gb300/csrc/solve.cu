@@ -351,7 +351,11 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
             RBF_CUDA_TRY(cudaMemcpyAsync(rr, sv.r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
             int its = 0;
             double est = 0.0;
-            st = sv.gmres(opts->inner_prec, rr, dl, true, eta * rn, opts->max_iters - it_c, &its, &est);
+            // each refinement step gets an equal share of the budget, so that the FP64
+            // residual judges a preconditioned step before the budget is gone
+            const int share = std::max(opts->restart_m, opts->max_iters / opts->max_refine);
+            const int budget = std::min(opts->max_iters - it_c, share);
+            st = sv.gmres(opts->inner_prec, rr, dl, true, eta * rn, budget, &its, &est);
             if (st != RBF_OK) break;
             it_c += its;
             last_used_p = sv.use_p;
