@@ -335,29 +335,26 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 192 : 256, sizeof(R) == 4 ? R
 // ------------------------------------------------------------------ M2M ---
 // Parents at level l from their children at level l+1 (child width wc).
 template <typename R>
-__global__ void k_m2m(int d, int M, int n1, int64_t nmode, int64_t ms, const R *xi, double wc,
+__global__ void k_m2m(int d, int M, int n1, int nmode, int64_t ms, const cplx<R> *sh,
                       const int32_t *child_off, const uint64_t *child_key, const cplx<R> *Vc,
                       cplx<R> *Vp)
 {
     using C = cplx<R>;
-    const int64_t m = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    const int m = blockIdx.y * blockDim.x + threadIdx.x;
     if (m >= nmode) return;
     const int p = blockIdx.x;
-    // per-dimension half shift e^{-i xi_k wc/2}
+    // per-dimension half shift e^{-i xi_k wc/2} (table row of the child level)
     C P[RBF_MAX_DIM];
-    int64_t r = m;
+    int r = m;
     for (int t = d - 1; t >= 0; --t) {
         int kidx;
         if (t > 0) {
-            kidx = (int)(r % n1);
+            kidx = r % n1;
             r /= n1;
         } else {
-            kidx = (int)r + M / 2;
+            kidx = r + M / 2;
         }
-        R s, co;
-        sincos_r(-xi[kidx] * (R)(0.5 * wc), &s, &co);
-        P[t].x = co;
-        P[t].y = s;
+        P[t] = sh[kidx];
     }
     C acc;
     acc.x = acc.y = (R)0;
@@ -472,40 +469,44 @@ __global__ void k_m2l(int d, int M, int D, int n1, int64_t nmode, int64_t ms, co
 // is summed one dimension at a time over the block, so each neighbour
 // expansion is read once per CTA instead of once per target.
 template <typename R, int DIM>
-__global__ void __launch_bounds__(128) k_m2l_grp(int M, int D, int n1, int64_t nmode, int64_t ms,
-                                                 const R *xi,
-                                                 const R *omegaC, double wD, const cplx<R> *root_ph,
+__global__ void __launch_bounds__(128) k_m2l_grp(int M, int D, int n1, int nmode, int64_t ms,
+                                                 const cplx<R> *shD,
+                                                 const R *omegaC, const cplx<R> *root_ph,
                                                  const uint64_t *parent_key, const int32_t *nb4,
                                                  const cplx<R> *V0, const cplx<R> *VD, cplx<R> *Lx)
 {
     using C = cplx<R>;
     constexpr int NB = DIM == 1 ? 4 : (DIM == 2 ? 16 : 64);
+    __shared__ const C *base[NB];   // expansion of each block position, or null
     __shared__ int32_t nb[NB];
     const int p = blockIdx.x;
-    for (int q = threadIdx.x; q < NB; q += blockDim.x) nb[q] = nb4[(int64_t)p * NB + q];
+    for (int q = threadIdx.x; q < NB; q += blockDim.x) {
+        const int32_t b = nb4[(int64_t)p * NB + q];
+        nb[q] = b;
+        base[q] = b >= 0 ? VD + (int64_t)b * ms : nullptr;
+    }
     __syncthreads();
-    const int64_t m = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    const int m = blockIdx.y * blockDim.x + threadIdx.x;
     if (m >= nmode) return;
     int kidx[3] = {0, 0, 0};
     {
-        int64_t r = m;
+        int r = m;
         for (int t = DIM - 1; t >= 1; --t) {
-            kidx[t] = (int)(r % n1);
+            kidx[t] = r % n1;
             r /= n1;
         }
-        kidx[0] = (int)r + M / 2;
+        kidx[0] = r + M / 2;
     }
+    // Q_t = e^{-i xi_k w_D} = (e^{-i xi_k w_D / 2})^2 from the plan's half-shift table
     C Q[3];
 #pragma unroll
     for (int t = 0; t < DIM; ++t) {
-        R sn, cs;
-        sincos_r(-xi[kidx[t]] * (R)wD, &sn, &cs);
-        Q[t].x = cs;
-        Q[t].y = sn;
+        const C hq = shD[kidx[t]];
+        Q[t] = cmul(hq, hq);
     }
     auto ld = [&](int pos) -> C {
-        const int b = nb[pos];
-        if (b >= 0) return VD[(int64_t)b * ms + m];
+        const C *bp = base[pos];
+        if (bp) return bp[m];
         C z;
         z.x = z.y = (R)0;
         return z;
@@ -717,7 +718,9 @@ int rbf_run_far(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaSt
     for (int l = D - 1; l >= 0; --l) {
         const double wc = t->side / (double)(1 << (l + 1));
         dim3 grid(t->lev[l].nbox, mchunks);
-        k_m2m<R><<<grid, mb, 0, s>>>(d, p->M, p->n1, p->nmode, p->mstride, (const R *)p->xi, wc,
+        (void)wc;
+        k_m2m<R><<<grid, mb, 0, s>>>(d, p->M, p->n1, (int)p->nmode, p->mstride,
+                                     (const C *)p->shift_ph + (int64_t)(l + 1) * p->n1,
                                      t->lev[l].child_off, t->lev[l + 1].key,
                                      (const C *)p->V[l + 1], (C *)p->V[l]);
         RBF_LAUNCH_CHECK();
@@ -726,13 +729,13 @@ int rbf_run_far(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaSt
     // coupling + downsweep at the leaves
     if (d <= 3) {
         rbf_pass_timer tm(t, RBF_PASS_M2L, s);
-        const double wD = t->side / (double)(1 << D);
         const int gb = 128;
         dim3 grid(t->lev[D - 1].nbox, ceil_div(p->nmode, gb));
         const C *V0 = (const C *)p->V[0], *VD = (const C *)p->V[D];
 #define RBF_M2L_GRP(DD)                                                                            \
-    k_m2l_grp<R, DD><<<grid, gb, 0, s>>>(p->M, D, p->n1, p->nmode, p->mstride, (const R *)p->xi,   \
-                                         (const R *)p->omegaC, wD, (const C *)p->root_ph,           \
+    k_m2l_grp<R, DD><<<grid, gb, 0, s>>>(p->M, D, p->n1, (int)p->nmode, p->mstride,                \
+                                         (const C *)p->shift_ph + (int64_t)D * p->n1,                \
+                                         (const R *)p->omegaC, (const C *)p->root_ph,                \
                                          t->lev[D - 1].key, t->nb4, V0, VD, (C *)p->Lleaf)
         if (d == 1) RBF_M2L_GRP(1);
         else if (d == 2) RBF_M2L_GRP(2);

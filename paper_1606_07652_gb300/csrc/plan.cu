@@ -143,6 +143,25 @@ __global__ void k_fill_root_ph(cplx<R> *ph, int d, int D, int M, double L, doubl
     ph[i].y = (R)s;
 }
 
+// shift_ph[l][j] = e^{-i xi_j w_l / 2}, w_l = side / 2^l, l = 0..D: the child-to-parent
+// centre shift of M2M at child level l is row l; the leaf-neighbour phase e^{-i xi w_D} is
+// the square of row D.
+template <typename R>
+__global__ void k_fill_shift_ph(cplx<R> *ph, int D, int M, double L, double side)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n1 = M + 1;
+    if (i >= (int64_t)(D + 1) * n1) return;
+    const int j = (int)(i % n1);
+    const int l = (int)(i / n1);
+    const double w = side / (double)((int64_t)1 << l);
+    const double xi = (j - M / 2) * (2.0 * M_PI / L);
+    double s, c;
+    sincos(-xi * 0.5 * w, &s, &c);
+    ph[i].x = (R)c;
+    ph[i].y = (R)s;
+}
+
 }  // namespace
 
 void rbf_default_params(rbf_kernel kernel, double side, rbf_fmm_params *p)
@@ -159,6 +178,7 @@ void rbf_plan_free(rbf_plan *p)
     rbf_free(p->omegaC);
     rbf_free(p->xi);
     rbf_free(p->root_ph);
+    rbf_free(p->shift_ph);
     for (int l = 0; l <= RBF_MAX_DEPTH; ++l) rbf_free(p->V[l]);
     rbf_free(p->Lleaf);
     rbf_free(p->lam_s);
@@ -213,6 +233,11 @@ static int build_tables(rbf_tree *t, rbf_plan *p, cudaStream_t s)
     RBF_TRY(rbf_alloc(reinterpret_cast<cplx<R> **>(&p->root_ph), nph));
     k_fill_root_ph<R><<<ceil_div(nph, 256), 256, 0, s>>>((cplx<R> *)p->root_ph, d, t->D, M, p->L,
                                                          t->side);
+    RBF_LAUNCH_CHECK();
+    // half shifts e^{-i xi w_l / 2} for every level l = 0..D (row l uses width side / 2^l)
+    const int64_t nsh = (int64_t)(t->D + 1) * (M + 1);
+    RBF_TRY(rbf_alloc(reinterpret_cast<cplx<R> **>(&p->shift_ph), nsh));
+    k_fill_shift_ph<R><<<ceil_div(nsh, 256), 256, 0, s>>>((cplx<R> *)p->shift_ph, t->D, M, p->L, t->side);
     RBF_LAUNCH_CHECK();
     RBF_CUDA_TRY(cudaStreamSynchronize(s));
     rbf_free(Chalf);
@@ -271,7 +296,8 @@ int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_param
         rbf_free(p->omegaC);
         rbf_free(p->xi);
         rbf_free(p->root_ph);
-        p->omegaC = p->xi = p->root_ph = nullptr;
+        rbf_free(p->shift_ph);
+        p->omegaC = p->xi = p->root_ph = p->shift_ph = nullptr;
     }
     p->prec = prec;
     p->kernel = kernel;

@@ -189,6 +189,8 @@ struct rbf_plan {
     void *omegaC = nullptr;    // [nmode] real: half-spectrum weight * omega * C
     void *xi = nullptr;        // [n1] real: xi_k, k = -M/2..M/2
     void *root_ph = nullptr;   // [d][2^D][n1] complex: e^{i xi_k (c_a,t - c_0,t)}
+    void *shift_ph = nullptr;  // [D+1][n1] complex: e^{-i xi_k w_l / 2}, w_l = side / 2^l
+                               // (row D doubled: e^{-i xi_k w_D}, the leaf-neighbour phase)
     void *V[RBF_MAX_DEPTH + 1] = {nullptr};  // expansions per level
     void *Lleaf = nullptr;     // local expansions at the leaves
     void *lam_s = nullptr;     // [N] gathered lambda
