@@ -1,0 +1,84 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times.
+
+The oracle cannot run the whole multilevel FMM at N = 2^20, so it computes sampled
+outputs one by one from the definition of what the FMM computes,
+    u_i = sum_{j near} lambda_j Phi(x_i - x_j) + sum_{j far} lambda_j K(x_i - x_j)
+(oracle.fmm_at_targets, pinned against the oracle's multilevel FMM in
+test_oracle_pins.py).  At every size the FP64 product must also satisfy the
+far-field bound of the scaled Lemma, Eq. (33), against the direct sum."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1606_07652_gb300 as rbf
+    rbf.load()
+    return rbf, torch
+
+
+def _gpu_products(rbf, torch, X, lam, depth, p):
+    t = rbf.tree_build(torch.as_tensor(X, device="cuda"), lo=np.zeros(X.shape[1]), side=1.0,
+                       depth=depth)
+    ld = torch.as_tensor(lam, device="cuda")
+    kw = dict(M=p["M"], period_L=p["L"], window_alpha=p["alpha"])
+    u64 = torch.empty_like(ld)
+    u32 = torch.empty_like(ld)
+    rbf.fmm_matvec(t, p["kernel"], p["eps"], ld, u64, prec=rbf.FP64, **kw)
+    rbf.fmm_matvec(t, p["kernel"], p["eps"], ld, u32, prec=rbf.FP32, **kw)
+    torch.cuda.synchronize()
+    return t, ld, u64.cpu().numpy(), u32.cpu().numpy()
+
+
+def test_bench_workload_sampled_parity_and_lemma_bound(env):
+    """3-D, N = 2^20 uniform, IMQ eps = 2, depth 5, M = 32, L = 4, alpha = 4.5 (bench.py)."""
+    rbf, torch = env
+    X, lam, targets, p = workloads.config2()
+    t, ld, u64, u32 = _gpu_products(rbf, torch, X, lam, p["depth"], p)
+    T = O.tree(X, np.zeros(3), 1.0, p["depth"])
+    wc = O.coeffs_sampled(p["kernel"], p["eps"], 3, p["M"], p["L"], p["alpha"], 1.0)
+    sample = targets[:12]
+    ref = O.fmm_at_targets(T, lam, p["kernel"], p["eps"], wc, p["M"], p["L"], sample)
+    e64 = np.linalg.norm(u64[sample] - ref) / np.linalg.norm(ref)
+    e32 = np.linalg.norm(u32[sample] - ref) / np.linalg.norm(ref)
+    print(f"N=2^20 sampled parity: fp64 {e64:.2e}  fp32 {e32:.2e}")
+    assert e64 <= 1e-12
+    assert e32 <= 5e-6
+    # Lemma (33): |u_fmm - u_direct|_i <= max_far |K - Phi| * sum_j |lambda_j|, on 4096 targets
+    tg = torch.as_tensor(np.asarray(targets, dtype=np.int64), device="cuda")
+    ud = torch.empty(len(targets), dtype=torch.float64, device="cuda")
+    rbf.direct_sum(torch.as_tensor(X, device="cuda"), p["kernel"], p["eps"], ld, tg, ud)
+    ud = ud.cpu().numpy()
+    rng = np.random.default_rng(21)
+    r = rng.uniform(-1, 1, (3000, 3))
+    r = r[np.max(np.abs(r), axis=1) >= 1.0 / 32]
+    kerr = np.max(np.abs(O.kernel_K(wc, 3, p["M"], p["L"], r)
+                         - O.phi(p["kernel"], p["eps"], np.linalg.norm(r, axis=1))))
+    bound = kerr * np.sum(np.abs(lam))
+    assert np.max(np.abs(u64[targets] - ud)) <= bound
+
+
+def test_clustered_workload_sampled_parity(env):
+    """3-D, N = 262,144 clustered (8 Gaussians), Gaussian eps = 3, depth 6, M = 24, L = 3:
+    leaves range from empty to ~90 points."""
+    rbf, torch = env
+    X, u, p = workloads.config3()
+    lam = np.random.default_rng(77).standard_normal(len(X))
+    t, ld, u64, u32 = _gpu_products(rbf, torch, X, lam, 6, p)
+    T = O.tree(X, np.zeros(3), 1.0, 6)
+    wc = O.coeffs_sampled(p["kernel"], p["eps"], 3, p["M"], p["L"], p["alpha"], 1.0)
+    sample = np.random.default_rng(78).choice(len(X), size=12, replace=False)
+    ref = O.fmm_at_targets(T, lam, p["kernel"], p["eps"], wc, p["M"], p["L"], sample)
+    e64 = np.linalg.norm(u64[sample] - ref) / np.linalg.norm(ref)
+    e32 = np.linalg.norm(u32[sample] - ref) / np.linalg.norm(ref)
+    print(f"clustered sampled parity: fp64 {e64:.2e}  fp32 {e32:.2e}")
+    assert e64 <= 1e-12
+    assert e32 <= 5e-6
