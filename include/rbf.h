@@ -150,10 +150,23 @@ RBF_API int rbf_tree_export_level(rbf_tree *t, int level, uint64_t *box_key, int
  *  params   expansion parameters (see rbf_fmm_params); NULL = defaults
  *           (M=32, L=4 side, alpha=4.5 for IMQ, 0 for Gaussian, csample=1).
  * Coefficient tables and expansion workspace are built on first use and kept
- * in the tree until the parameters change.  Asynchronous. */
+ * in the tree until the parameters change.  Asynchronous.
+ * With RBF_FP32 and nrhs >= RBF_MULTI_RHS_MIN the columns go through the far
+ * field G at a time (G <= 16, bounded by min(64 GB, half the free device
+ * memory) of expansion workspace): P2M and L2P of the G columns are complex
+ * matrix products on the tensor cores (three-term split TF32 operands, FP32
+ * accumulation), the translations run per column.  Check
+ * rbf_check_device_waits after such calls when a bounded device wait must be
+ * ruled out. */
+#define RBF_MULTI_RHS_MIN 4
 RBF_API int rbf_fmm_matvec(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_params *params,
                    rbf_precision prec, const double *lambda, int64_t ld_lambda, double *u,
                    int64_t ld_u, int nrhs, void *stream);
+
+/* Synchronises the device and reports whether a bounded wait inside a
+ * tensor-core kernel gave up since the previous call (RBF_ETIMEOUT, with the
+ * kernel's results left incomplete) or not (RBF_OK).  Clears the record. */
+RBF_API int rbf_check_device_waits(void);
 
 /* Same product with host buffers: copies lambda_host to the device, runs
  * rbf_fmm_matvec, copies u back.  Synchronises `stream`. */

@@ -88,6 +88,7 @@ def load():
     lib.rbf_tree_export_level.argtypes = [_c_vp, _c_int, _c_vp, _c_vp, _c_vp, P(_c_i64), _c_vp]
     lib.rbf_fmm_matvec.argtypes = [_c_vp, _c_int, _c_dbl, P(FmmParams), _c_int, _c_vp, _c_i64,
                                    _c_vp, _c_i64, _c_int, _c_vp]
+    lib.rbf_check_device_waits.argtypes = []
     lib.rbf_fmm_matvec_host.argtypes = [_c_vp, _c_int, _c_dbl, P(FmmParams), _c_int, _c_vp,
                                         _c_vp, _c_int, _c_vp]
     lib.rbf_direct_sum.argtypes = [_c_vp, _c_i64, _c_int, _c_int, _c_dbl, _c_vp, _c_vp, _c_i64,
@@ -258,6 +259,11 @@ def fmm_matvec(tree: Tree, kernel: int, eps: float, lam, u, prec=FP64, M=None, p
                                  _dev(lam, "float64", "lam"), N, _dev(u, "float64", "u"), N, nrhs,
                                  _stream()), "rbf_fmm_matvec")
     return u
+
+
+def check_device_waits():
+    """rbf_check_device_waits: raises when a bounded wait of a tensor-core kernel gave up."""
+    _check(load().rbf_check_device_waits(), "rbf_check_device_waits")
 
 
 def _host_ptr(a, where):

@@ -613,6 +613,102 @@ __global__ void __launch_bounds__(128) k_m2l_grp(int M, int D, int n1, int nmode
     }
 }
 
+// Coupling on the whole leaf grid, for small grids (S = 2^D boxes per
+// dimension, S^d <= 4096): the neighbour sum of the telescoped coupling,
+//   S_a = sum_{b in N_a} e^{i xi.(c_a - c_b)} V_b,
+// is a separable three-tap stencil over the grid (absent boxes hold zero),
+// applied one dimension at a time to MC consecutive modes held in shared
+// memory; then L_a = omega C (e^{i xi.(c_a - c_0)} V_0 - S_a).  Each leaf
+// expansion is read once and each local expansion written once.
+template <typename R, int S>
+__global__ void __launch_bounds__(256) k_m2l_full(int d, int M, int n1, int64_t nmode, int64_t ms,
+                                                  int MC, int nleaf, const R *omegaC,
+                                                  const cplx<R> *shD, const cplx<R> *root_ph,
+                                                  const uint64_t *leaf_key, const cplx<R> *V0,
+                                                  const cplx<R> *VD, cplx<R> *Lx)
+{
+    using C = cplx<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *grid = reinterpret_cast<C *>(smem_raw);              // [nbox][MC]
+    int *kid = reinterpret_cast<int *>(grid + 0);            // placeholder, set below
+    int nbox = 1;
+    for (int t = 0; t < d; ++t) nbox *= S;
+    kid = reinterpret_cast<int *>(grid + (int64_t)nbox * MC);  // [d][MC] frequency index
+    const int64_t m0 = (int64_t)blockIdx.x * MC;
+    const int mc = (int)min((int64_t)MC, nmode - m0);
+    const int D = __ffs(S) - 1;
+    for (int q = threadIdx.x; q < d * MC; q += blockDim.x) {
+        const int t = q / MC, mm = q - t * MC;
+        int64_t r = m0 + min(mm, mc - 1);
+        int k = 0;
+        for (int u = d - 1; u >= 0; --u) {
+            if (u == 0) {
+                k = (int)r + M / 2;
+            } else {
+                const int dig = (int)(r % n1);
+                r /= n1;
+                if (u == t) k = dig;
+            }
+            if (u == t) break;
+        }
+        kid[q] = k;
+    }
+    for (int q = threadIdx.x; q < nbox * MC; q += blockDim.x) grid[q] = C{(R)0, (R)0};
+    __syncthreads();
+    for (int q = threadIdx.x; q < nleaf * MC; q += blockDim.x) {
+        const int l = q / MC, mm = q - l * MC;
+        if (mm >= mc) continue;
+        int k[RBF_MAX_DIM];
+        decode_key(leaf_key[l], d, D, k);
+        int g = 0;
+        for (int t = d - 1; t >= 0; --t) g = g * S + k[t];
+        grid[g * MC + mm] = VD[(int64_t)l * ms + m0 + mm];
+    }
+    __syncthreads();
+    int stride = 1;
+    for (int t = 0; t < d; ++t) {
+        const int nline = nbox / S;
+        for (int q = threadIdx.x; q < nline * MC; q += blockDim.x) {
+            const int line = q / MC, mm = q - line * MC;
+            const int lo = line % stride, hi = line / stride;
+            C *base = grid + ((int64_t)lo + (int64_t)hi * stride * S) * MC + mm;
+            // e^{-i xi_k w_D}: factor of the neighbour one box up, conj for one box down
+            const C h = shD[kid[t * MC + mm]];
+            const C qf = cmul(h, h);
+            C v[S];
+#pragma unroll
+            for (int i = 0; i < S; ++i) v[i] = base[(int64_t)i * stride * MC];
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                C o = v[i];
+                if (i > 0) cmac(o, cconj(qf), v[i - 1]);
+                if (i + 1 < S) cmac(o, qf, v[i + 1]);
+                base[(int64_t)i * stride * MC] = o;
+            }
+        }
+        stride *= S;
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < nleaf * MC; q += blockDim.x) {
+        const int l = q / MC, mm = q - l * MC;
+        if (mm >= mc) continue;
+        int k[RBF_MAX_DIM];
+        decode_key(leaf_key[l], d, D, k);
+        int g = 0;
+        for (int t = d - 1; t >= 0; --t) g = g * S + k[t];
+        const int64_t m = m0 + mm;
+        C ph = root_ph[(int64_t)k[0] * n1 + kid[mm]];
+        for (int t = 1; t < d; ++t) ph = cmul(ph, root_ph[((int64_t)t * S + k[t]) * n1 + kid[t * MC + mm]]);
+        const C r = cmul(ph, V0[m]);
+        const C sa = grid[g * MC + mm];
+        const R w = omegaC[m];
+        C out;
+        out.x = w * (r.x - sa.x);
+        out.y = w * (r.y - sa.y);
+        Lx[(int64_t)l * ms + m] = out;
+    }
+}
+
 // block size: multiple of 32*NH threads, fewest idle row slots
 inline int pick_block(int nrow, int rpt, int nh, int bmax)
 {
@@ -675,16 +771,91 @@ int dispatch_p2m_l2p(bool l2p, const FarArgs<R> &a, int nleaf, cudaStream_t s)
 
 }  // namespace
 
+// M2M from the leaf expansions VD up to the root (levels D-1 .. 0 of the plan)
 template <typename R>
-int rbf_run_far(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStream_t s)
+int rbf_run_m2m(rbf_tree *t, const rbf_plan *p, const cplx<R> *VD, cudaStream_t s)
 {
     using C = cplx<R>;
     const int d = t->d, D = t->D;
-    const int nleaf = t->nleaf();
+    const int mb = 256;
+    const int mchunks = ceil_div(p->nmode, mb);
+    RBF_REQUIRE(mchunks < 65536, "expansion too large (%lld modes)", (long long)p->nmode);
+    rbf_pass_timer tm(t, RBF_PASS_M2M, s, D);
+    for (int l = D - 1; l >= 0; --l) {
+        dim3 grid(t->lev[l].nbox, mchunks);
+        const C *child = l + 1 == D ? VD : (const C *)p->V[l + 1];
+        k_m2m<R><<<grid, mb, 0, s>>>(d, p->M, p->n1, (int)p->nmode, p->mstride,
+                                     (const C *)p->shift_ph + (int64_t)(l + 1) * p->n1,
+                                     t->lev[l].child_off, t->lev[l + 1].key, child, (C *)p->V[l]);
+        RBF_LAUNCH_CHECK();
+    }
+    return RBF_OK;
+}
+
+// coupling of all levels plus the downsweep: leaf local expansions L from the
+// leaf expansions VD and the root expansion V[0] (left by rbf_run_m2m)
+template <typename R>
+int rbf_run_m2l(rbf_tree *t, const rbf_plan *p, const cplx<R> *VD, cplx<R> *L, cudaStream_t s)
+{
+    using C = cplx<R>;
+    const int d = t->d, D = t->D;
+    rbf_pass_timer tm(t, RBF_PASS_M2L, s);
+    const C *V0 = (const C *)p->V[0];
+    if (d <= 3) {
+        const int gb = 128;
+        dim3 grid(t->lev[D - 1].nbox, ceil_div(p->nmode, gb));
+#define RBF_M2L_GRP(DD)                                                                            \
+    k_m2l_grp<R, DD><<<grid, gb, 0, s>>>(p->M, D, p->n1, (int)p->nmode, p->mstride,                \
+                                         (const C *)p->shift_ph + (int64_t)D * p->n1,                \
+                                         (const R *)p->omegaC, (const C *)p->root_ph,                \
+                                         t->lev[D - 1].key, t->nb4, V0, VD, L)
+        if (d == 1) RBF_M2L_GRP(1);
+        else if (d == 2) RBF_M2L_GRP(2);
+        else RBF_M2L_GRP(3);
+#undef RBF_M2L_GRP
+        RBF_LAUNCH_CHECK();
+    } else if (D >= 2 && D <= 4 && d * D <= 12) {
+        // whole leaf grid of S^d <= 4096 boxes: MC modes per CTA within 96 KB
+        const int S = 1 << D;
+        const int64_t nbox = (int64_t)1 << (d * D);
+        const int MC = (int)std::max<int64_t>(1, std::min<int64_t>(16, (96 * 1024) / (nbox * (int64_t)sizeof(C))));
+        const size_t smem = (size_t)nbox * MC * sizeof(C) + (size_t)d * MC * sizeof(int);
+        const int nblk = ceil_div(p->nmode, MC);
+#define RBF_M2L_FULL(SS)                                                                          \
+    do {                                                                                          \
+        RBF_CUDA_TRY(cudaFuncSetAttribute(k_m2l_full<R, SS>,                                      \
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        k_m2l_full<R, SS><<<nblk, 256, smem, s>>>(d, p->M, p->n1, p->nmode, p->mstride, MC,       \
+                                                  t->nleaf(), (const R *)p->omegaC,              \
+                                                  (const C *)p->shift_ph + (int64_t)D * p->n1,    \
+                                                  (const C *)p->root_ph, t->leaf_key(), V0, VD, L); \
+    } while (0)
+        if (S == 4) RBF_M2L_FULL(4);
+        else if (S == 8) RBF_M2L_FULL(8);
+        else RBF_M2L_FULL(16);
+#undef RBF_M2L_FULL
+        RBF_LAUNCH_CHECK();
+    } else {
+        const int mb = 256;
+        const double wD = t->side / (double)(1 << D);
+        dim3 grid(t->nleaf(), ceil_div(p->nmode, mb));
+        RBF_REQUIRE(grid.y < 65536, "expansion too large (%lld modes)", (long long)p->nmode);
+        k_m2l<R><<<grid, mb, 0, s>>>(d, p->M, D, p->n1, p->nmode, p->mstride, (const R *)p->xi,
+                                     (const R *)p->omegaC, wD, (const C *)p->root_ph, t->leaf_key(),
+                                     t->near_off, t->near_idx, V0, VD, L);
+        RBF_LAUNCH_CHECK();
+    }
+    return RBF_OK;
+}
+
+namespace {
+template <typename R>
+FarArgs<R> far_args(const rbf_tree *t, const rbf_plan *p)
+{
     FarArgs<R> a;
-    a.d = d;
+    a.d = t->d;
     a.M = p->M;
-    a.D = D;
+    a.D = t->D;
     a.n0 = p->n0;
     a.n1 = p->n1;
     a.nrow = p->nrow;
@@ -695,71 +866,57 @@ int rbf_run_far(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaSt
     for (int q = 0; q < RBF_MAX_DIM; ++q) a.lo[q] = t->lo[q];
     a.side = t->side;
     a.xs = (const R *)(sizeof(R) == 8 ? (const void *)t->xs64 : (const void *)t->xs32);
-    a.lam = lam_s;
+    a.lam = nullptr;
     a.leaf_off = t->leaf_off;
     a.leaf_key = t->leaf_key();
     a.xi = (const R *)p->xi;
-    a.V = (C *)p->V[D];
-    a.Lx = (const C *)p->Lleaf;
-    a.u = u_far;
+    a.V = nullptr;
+    a.Lx = nullptr;
+    a.u = nullptr;
     a.pch = 0;   // set per launch: as many points as fit in ~64 KB of tables, at most 64
     a.seg0 = a.seg = 0;
-    // P2M at the leaves
-    {
-        rbf_pass_timer tm(t, RBF_PASS_P2M, s);
-        RBF_TRY(dispatch_p2m_l2p<R>(false, a, nleaf, s));
-    }
-    // M2M up to the root
-    const int mb = 256;
-    const int mchunks = ceil_div(p->nmode, mb);
-    RBF_REQUIRE(mchunks < 65536, "expansion too large (%lld modes)", (long long)p->nmode);
-    {
-    rbf_pass_timer tm(t, RBF_PASS_M2M, s, D);
-    for (int l = D - 1; l >= 0; --l) {
-        const double wc = t->side / (double)(1 << (l + 1));
-        dim3 grid(t->lev[l].nbox, mchunks);
-        (void)wc;
-        k_m2m<R><<<grid, mb, 0, s>>>(d, p->M, p->n1, (int)p->nmode, p->mstride,
-                                     (const C *)p->shift_ph + (int64_t)(l + 1) * p->n1,
-                                     t->lev[l].child_off, t->lev[l + 1].key,
-                                     (const C *)p->V[l + 1], (C *)p->V[l]);
-        RBF_LAUNCH_CHECK();
-    }
-    }
-    // coupling + downsweep at the leaves
-    if (d <= 3) {
-        rbf_pass_timer tm(t, RBF_PASS_M2L, s);
-        const int gb = 128;
-        dim3 grid(t->lev[D - 1].nbox, ceil_div(p->nmode, gb));
-        const C *V0 = (const C *)p->V[0], *VD = (const C *)p->V[D];
-#define RBF_M2L_GRP(DD)                                                                            \
-    k_m2l_grp<R, DD><<<grid, gb, 0, s>>>(p->M, D, p->n1, (int)p->nmode, p->mstride,                \
-                                         (const C *)p->shift_ph + (int64_t)D * p->n1,                \
-                                         (const R *)p->omegaC, (const C *)p->root_ph,                \
-                                         t->lev[D - 1].key, t->nb4, V0, VD, (C *)p->Lleaf)
-        if (d == 1) RBF_M2L_GRP(1);
-        else if (d == 2) RBF_M2L_GRP(2);
-        else RBF_M2L_GRP(3);
-#undef RBF_M2L_GRP
-        RBF_LAUNCH_CHECK();
-    } else {
-        rbf_pass_timer tm(t, RBF_PASS_M2L, s);
-        const double wD = t->side / (double)(1 << D);
-        dim3 grid(nleaf, mchunks);
-        k_m2l<R><<<grid, mb, 0, s>>>(d, p->M, D, p->n1, p->nmode, p->mstride, (const R *)p->xi,
-                                     (const R *)p->omegaC, wD, (const C *)p->root_ph, t->leaf_key(),
-                                     t->near_off, t->near_idx, (const C *)p->V[0],
-                                     (const C *)p->V[D], (C *)p->Lleaf);
-        RBF_LAUNCH_CHECK();
-    }
-    // L2P
-    {
-        rbf_pass_timer tm(t, RBF_PASS_L2P, s);
-        RBF_TRY(dispatch_p2m_l2p<R>(true, a, nleaf, s));
-    }
+    return a;
+}
+}  // namespace
+
+// P2M of one column into the leaf expansions V (nleaf x mstride)
+template <typename R>
+int rbf_run_p2m(rbf_tree *t, const rbf_plan *p, const R *lam_s, cplx<R> *V, cudaStream_t s)
+{
+    FarArgs<R> a = far_args<R>(t, p);
+    a.lam = lam_s;
+    a.V = V;
+    rbf_pass_timer tm(t, RBF_PASS_P2M, s);
+    return dispatch_p2m_l2p<R>(false, a, t->nleaf(), s);
+}
+
+// L2P of one column from the leaf local expansions L
+template <typename R>
+int rbf_run_l2p(rbf_tree *t, const rbf_plan *p, const cplx<R> *L, R *u_far, cudaStream_t s)
+{
+    FarArgs<R> a = far_args<R>(t, p);
+    a.Lx = L;
+    a.u = u_far;
+    rbf_pass_timer tm(t, RBF_PASS_L2P, s);
+    return dispatch_p2m_l2p<R>(true, a, t->nleaf(), s);
+}
+
+template <typename R>
+int rbf_run_far(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStream_t s)
+{
+    using C = cplx<R>;
+    const int D = t->D;
+    RBF_TRY(rbf_run_p2m<R>(t, p, lam_s, (C *)p->V[D], s));
+    RBF_TRY(rbf_run_m2m<R>(t, p, (const C *)p->V[D], s));
+    RBF_TRY(rbf_run_m2l<R>(t, p, (const C *)p->V[D], (C *)p->Lleaf, s));
+    RBF_TRY(rbf_run_l2p<R>(t, p, (const C *)p->Lleaf, u_far, s));
     return RBF_OK;
 }
 
 template int rbf_run_far<float>(rbf_tree *, const rbf_plan *, const float *, float *, cudaStream_t);
+template int rbf_run_m2m<float>(rbf_tree *, const rbf_plan *, const float2 *, cudaStream_t);
+template int rbf_run_p2m<float>(rbf_tree *, const rbf_plan *, const float *, float2 *, cudaStream_t);
+template int rbf_run_l2p<float>(rbf_tree *, const rbf_plan *, const float2 *, float *, cudaStream_t);
+template int rbf_run_m2l<float>(rbf_tree *, const rbf_plan *, const float2 *, float2 *, cudaStream_t);
 template int rbf_run_far<double>(rbf_tree *, const rbf_plan *, const double *, double *,
                                  cudaStream_t);

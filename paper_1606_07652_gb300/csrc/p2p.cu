@@ -192,6 +192,163 @@ int launch_p2p(int d, int kernel, R e2, const rbf_tree *t, const R *xs, const R 
     return RBF_OK;
 }
 
+// ---------------------------------------------- several right-hand sides --
+// The near field of RG columns at once: Phi(x_i - x_j) is evaluated once per
+// pair and multiplies the RG coefficients of the source.  Sources are staged
+// as records (coordinates padded to 4 or 8 floats, then RG coefficients);
+// lane = target, TG targets per lane, warps split the staged sources and their
+// partial sums are added in a fixed order.
+constexpr int P2PM_SCH = 256;   // sources per staged chunk
+
+template <int DIM, int RG>
+struct P2pmShape {
+    static constexpr int C4 = DIM <= 4 ? 4 : 8;            // padded coordinates
+    static constexpr int REC = C4 + RG;                    // floats per source record
+    static constexpr int TG = RG >= 16 ? 4 : 4;            // target groups of 32 per pass
+    static constexpr int TB = 32 * TG;
+    static constexpr int STAGE = P2PM_SCH * REC;
+    static constexpr int RED = P2P_WARPS * TB * RG;
+    static constexpr int BUF = STAGE > RED ? STAGE : RED;
+};
+
+template <int DIM, int RG>
+__global__ void __launch_bounds__(P2P_THREADS) k_p2p_multi(int kernel, float e2, int64_t N,
+                                                           const float *xs, const float *lam,
+                                                           int G, const int32_t *leaf_off,
+                                                           const int32_t *near_off,
+                                                           const int32_t *near_idx, float *u)
+{
+    using SH = P2pmShape<DIM, RG>;
+    constexpr int C4 = SH::C4, REC = SH::REC, TG = SH::TG, TB = SH::TB;
+    __shared__ __align__(16) float buf[SH::BUF];
+    __shared__ int32_t rstart[729], rpre[730];
+    const int a = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int e0 = near_off[a], ne = near_off[a + 1] - e0;
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int e = 0; e < ne; ++e) {
+            const int b = near_idx[e0 + e];
+            rstart[e] = leaf_off[b];
+            rpre[e] = run;
+            run += leaf_off[b + 1] - leaf_off[b];
+        }
+        rpre[ne] = run;
+    }
+    __syncthreads();
+    const int nsrc = rpre[ne];
+    const int t0 = leaf_off[a], nt = leaf_off[a + 1] - t0;
+    for (int tb = 0; tb < nt; tb += TB) {
+        float xt[TG][DIM];
+        float acc[TG][RG];
+#pragma unroll
+        for (int g = 0; g < TG; ++g) {
+            const int i = tb + g * 32 + lane;
+#pragma unroll
+            for (int t = 0; t < DIM; ++t) xt[g][t] = i < nt ? xs[(int64_t)t * N + t0 + i] : 0.0f;
+#pragma unroll
+            for (int r = 0; r < RG; ++r) acc[g][r] = 0.0f;
+        }
+        const int ngrp = min(TG, (nt - tb + 31) / 32);
+        for (int s0 = 0; s0 < nsrc; s0 += P2PM_SCH) {
+            const int cnt = min(P2PM_SCH, nsrc - s0);
+            __syncthreads();
+            for (int v = threadIdx.x; v < cnt; v += P2P_THREADS) {
+                const int vv = s0 + v;
+                int lo = 0, hi = ne - 1;
+                while (lo < hi) {  // last range with rpre[e] <= vv
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (rpre[mid] <= vv) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int64_t j = rstart[lo] + (vv - rpre[lo]);
+                float *rec = buf + v * REC;
+#pragma unroll
+                for (int t = 0; t < C4; ++t) rec[t] = t < DIM ? xs[(int64_t)t * N + j] : 0.0f;
+#pragma unroll
+                for (int r = 0; r < RG; ++r) rec[C4 + r] = r < G ? lam[(int64_t)r * N + j] : 0.0f;
+            }
+            __syncthreads();
+            for (int j = warp; j < cnt; j += P2P_WARPS) {
+                const float4 *rec = reinterpret_cast<const float4 *>(buf + j * REC);
+                float xs_[C4], l[RG];
+#pragma unroll
+                for (int c = 0; c < C4 / 4; ++c) {
+                    const float4 v = rec[c];
+                    xs_[4 * c] = v.x;
+                    xs_[4 * c + 1] = v.y;
+                    xs_[4 * c + 2] = v.z;
+                    xs_[4 * c + 3] = v.w;
+                }
+#pragma unroll
+                for (int c = 0; c < RG / 4; ++c) {
+                    const float4 v = rec[C4 / 4 + c];
+                    l[4 * c] = v.x;
+                    l[4 * c + 1] = v.y;
+                    l[4 * c + 2] = v.z;
+                    l[4 * c + 3] = v.w;
+                }
+#pragma unroll
+                for (int g = 0; g < TG; ++g) {
+                    if (g < ngrp) {
+                        float r2 = 0.0f;
+#pragma unroll
+                        for (int t = 0; t < DIM; ++t) {
+                            const float df = xt[g][t] - xs_[t];
+                            r2 = fmaf(df, df, r2);
+                        }
+                        const float ph = phi_r2(kernel, e2, r2);
+#pragma unroll
+                        for (int r = 0; r < RG; ++r) acc[g][r] = fmaf(l[r], ph, acc[g][r]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // partial sums of the warps -> fixed-order total
+#pragma unroll
+        for (int g = 0; g < TG; ++g)
+#pragma unroll
+            for (int r = 0; r < RG; ++r) buf[(warp * TB + g * 32 + lane) * RG + r] = acc[g][r];
+        __syncthreads();
+        const int nb = min(TB, nt - tb);
+        for (int idx = threadIdx.x; idx < nb * G; idx += P2P_THREADS) {
+            const int r = idx / nb, i = idx - r * nb;
+            float sum = buf[i * RG + r];
+#pragma unroll
+            for (int w = 1; w < P2P_WARPS; ++w) sum += buf[(w * TB + i) * RG + r];
+            u[(int64_t)r * N + t0 + tb + i] = sum;
+        }
+    }
+}
+
+template <int RG>
+int launch_p2p_multi(int d, int kernel, float e2, const rbf_tree *t, const float *lam, int G,
+                     float *u, cudaStream_t s)
+{
+    const int nleaf = t->nleaf();
+    switch (d) {
+#define RBF_P2PM_CASE(DD)                                                                         \
+    case DD:                                                                                      \
+        k_p2p_multi<DD, RG><<<nleaf, P2P_THREADS, 0, s>>>(kernel, e2, t->N, t->xs32, lam, G,      \
+                                                          t->leaf_off, t->near_off, t->near_idx,  \
+                                                          u);                                     \
+        break;
+        RBF_P2PM_CASE(1)
+        RBF_P2PM_CASE(2)
+        RBF_P2PM_CASE(3)
+        RBF_P2PM_CASE(4)
+        RBF_P2PM_CASE(5)
+        RBF_P2PM_CASE(6)
+#undef RBF_P2PM_CASE
+        default:
+            rbf_set_error("p2p: unsupported dimension %d", d);
+            return RBF_EINVAL;
+    }
+    RBF_LAUNCH_CHECK();
+    return RBF_OK;
+}
+
 // ------------------------------------------------------- direct sum -------
 constexpr int DS_THREADS = 256;
 constexpr int DS_TILE = 256;
@@ -242,6 +399,18 @@ int rbf_run_p2p(rbf_tree *t, int kernel, double eps, const R *lam_s, R *u, cudaS
 }
 
 template int rbf_run_p2p<float>(rbf_tree *, int, double, const float *, float *, cudaStream_t);
+
+int rbf_run_p2p_multi(rbf_tree *t, int kernel, double eps, const float *lam_s, int G, float *u,
+                      cudaStream_t s)
+{
+    RBF_REQUIRE(G >= 1 && G <= 16, "rbf_run_p2p_multi: G=%d", G);
+    rbf_pass_timer tm(t, RBF_PASS_P2P, s);
+    double e2 = eps * eps;
+    if (kernel == RBF_GAUSSIAN) e2 *= 1.4426950408889634;
+    if (G <= 4) return launch_p2p_multi<4>(t->d, kernel, (float)e2, t, lam_s, G, u, s);
+    if (G <= 8) return launch_p2p_multi<8>(t->d, kernel, (float)e2, t, lam_s, G, u, s);
+    return launch_p2p_multi<16>(t->d, kernel, (float)e2, t, lam_s, G, u, s);
+}
 template int rbf_run_p2p<double>(rbf_tree *, int, double, const double *, double *,
                                  cudaStream_t);
 

@@ -184,6 +184,11 @@ void rbf_plan_free(rbf_plan *p)
     rbf_free(p->lam_s);
     rbf_free(p->u_near);
     rbf_free(p->u_far);
+    rbf_free(p->mr_V);
+    rbf_free(p->mr_L);
+    rbf_free(p->mr_lam);
+    rbf_free(p->mr_un);
+    rbf_free(p->mr_uf);
     delete p;
 }
 

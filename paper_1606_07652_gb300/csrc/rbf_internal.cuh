@@ -190,13 +190,21 @@ struct rbf_plan {
     void *xi = nullptr;        // [n1] real: xi_k, k = -M/2..M/2
     void *root_ph = nullptr;   // [d][2^D][n1] complex: e^{i xi_k (c_a,t - c_0,t)}
     void *shift_ph = nullptr;  // [D+1][n1] complex: e^{-i xi_k w_l / 2}, w_l = side / 2^l
-                               // (row D doubled: e^{-i xi_k w_D}, the leaf-neighbour phase)
+                               // (the square of row D is the leaf-neighbour phase e^{-i xi_k w_D})
     void *V[RBF_MAX_DEPTH + 1] = {nullptr};  // expansions per level
     void *Lleaf = nullptr;     // local expansions at the leaves
     void *lam_s = nullptr;     // [N] gathered lambda
     void *u_near = nullptr;    // [N]
     void *u_far = nullptr;     // [N]
     size_t bytes = 0;
+    // multi-right-hand-side workspace (FP32 plans only), grown on demand:
+    // mr_G columns at a time, each with its own leaf and local expansions
+    int mr_G = 0;
+    float2 *mr_V = nullptr;    // [mr_G][nleaf][mstride]
+    float2 *mr_L = nullptr;    // [mr_G][nleaf][mstride]
+    float *mr_lam = nullptr;   // [mr_G][N]
+    float *mr_un = nullptr;    // [mr_G][N]
+    float *mr_uf = nullptr;    // [mr_G][N]
 };
 
 int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_params *p, int prec,
@@ -208,6 +216,27 @@ template <typename R>
 int rbf_run_p2p(rbf_tree *t, int kernel, double eps, const R *lam_s, R *u, cudaStream_t s);
 template <typename R>
 int rbf_run_far(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStream_t s);
+// FP32 near field of G <= 16 columns at once (lam_s, u: [G][N])
+int rbf_run_p2p_multi(rbf_tree *t, int kernel, double eps, const float *lam_s, int G, float *u,
+                      cudaStream_t s);
+// P2M and L2P of one column on explicit leaf arrays (CUDA cores)
+template <typename R>
+int rbf_run_p2m(rbf_tree *t, const rbf_plan *p, const R *lam_s, cplx<R> *V, cudaStream_t s);
+template <typename R>
+int rbf_run_l2p(rbf_tree *t, const rbf_plan *p, const cplx<R> *L, R *u_far, cudaStream_t s);
+// the translation passes on explicit leaf arrays (V[0..D-1] of the plan are scratch)
+template <typename R>
+int rbf_run_m2m(rbf_tree *t, const rbf_plan *p, const cplx<R> *VD, cudaStream_t s);
+template <typename R>
+int rbf_run_m2l(rbf_tree *t, const rbf_plan *p, const cplx<R> *VD, cplx<R> *L, cudaStream_t s);
+// FP32 far field of G right-hand sides at once: P2M and L2P on the tensor cores
+// (far_mrhs.cu); lam_s and u_far are [G][N], V and L are [G][nleaf][mstride]
+int rbf_run_far_multi(rbf_tree *t, const rbf_plan *p, const float *lam_s, int G, float2 *V,
+                      float2 *L, float *u_far, cudaStream_t s);
+// nonzero when the plan's columns per mode row fit a tensor-core tile
+int rbf_far_multi_supported(const rbf_plan *p);
+// nonzero when a bounded device-side wait of a tensor-core kernel gave up
+int rbf_tc_fetch_status(int *flags_host);
 
 // Internal product on sorted-order device vectors (FP64 in/out, any arithmetic);
 // used by the matvec entry point and the solver.

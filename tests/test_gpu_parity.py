@@ -97,6 +97,8 @@ MATVEC_CASES = [
     ("depth2", 3, 2000, 2, O.GAUSSIAN, 3.0, 12, 3.0, 0.0, "u"),
     ("1d", 1, 3000, 4, O.IMQ, 3.0, 24, 4.0, 4.5, "u"),
     ("5d", 5, 1500, 2, O.GAUSSIAN, 1.5, 4, 4.0, 0.0, "u"),
+    ("4d-depth3-grid", 4, 3000, 3, O.GAUSSIAN, 2.0, 6, 4.0, 0.0, "u"),
+    ("6d", 6, 700, 2, O.IMQ, 1.0, 4, 4.0, 4.5, "u"),
 ]
 
 
