@@ -44,8 +44,9 @@ def _peaks():
         with open(path) as f:
             p = json.load(f)
         return {"hbm_gbs": p["hbm_gbs"], "sm_max_mhz": p.get("sm_max_mhz", 2070.0),
-                "source": "measured"}
-    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+                "bf16_tflops": p.get("bf16_tflops", 1900.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "bf16_tflops": 1900.0,
+            "source": "fallback"}
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -272,6 +273,8 @@ def run_ours(args):
             out["batch"] = batch_measurement(rbf, dev)
         if args.solve:
             out["solve"] = solve_measurement(rbf, dev)
+        if args.mrhs:
+            out["multi_rhs"] = multi_rhs_measurement(rbf, dev)
         if not args.skip_cpu and world == 1:
             out["cpu_baseline"] = cpu_baseline(X, lam, p, budget_s=args.cpu_budget)
     if dist:
@@ -397,6 +400,85 @@ def solve_measurement(rbf, dev):
     return res
 
 
+def multi_rhs_measurement(rbf, dev, tol=1.5e-7, nrhs=16):
+    """d = 5, N = 2^19 uniform, Gaussian eps = 1.5, depth 2 (512 points per leaf), L = 4,
+    M = the smallest even M whose measured far-kernel error is <= 1.5e-7.  Times one FP32
+    product of a single column and one of the 16-column block (P2M and L2P of the block on
+    the tensor cores, one multi-column near-field pass), checks the single column against
+    the FP64 direct sum on 2048 targets and the block against single-column products."""
+    import torch
+    import workloads
+    from paper_1606_07652_gb300 import _lib
+    X, lam, lamb, targets, p = workloads.config5(nrhs=nrhs)
+    N = len(X)
+    M = 8
+    err_k = _lib.kernel_error(p["kernel"], p["eps"], 5, M, p["L"], 0.0, 1.0, p["depth"])
+    while err_k > tol and M < 24:
+        M += 2
+        err_k = _lib.kernel_error(p["kernel"], p["eps"], 5, M, p["L"], 0.0, 1.0, p["depth"])
+    Xd = torch.as_tensor(X, device=dev)
+    t = rbf.tree_build(Xd, lo=np.zeros(5), side=1.0, depth=p["depth"])
+    kw = dict(M=M, period_L=p["L"], window_alpha=0.0, prec=rbf.FP32)
+    ld = torch.as_tensor(lam, device=dev)
+    u = torch.empty_like(ld)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rbf.fmm_matvec(t, p["kernel"], p["eps"], ld, u, **kw)
+    torch.cuda.synchronize()
+    e0.record()
+    rbf.fmm_matvec(t, p["kernel"], p["eps"], ld, u, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    tg = torch.as_tensor(np.asarray(targets, dtype=np.int64), device=dev)
+    ud = torch.empty(len(targets), dtype=torch.float64, device=dev)
+    rbf.direct_sum(Xd, p["kernel"], p["eps"], ld, tg, ud)
+    torch.cuda.synchronize()
+    err1 = float((u[tg] - ud).norm() / ud.norm())
+    Lb = torch.as_tensor(np.ascontiguousarray(lamb.T), device=dev)      # (nrhs, N)
+    Ub = torch.empty_like(Lb)
+    rbf.fmm_matvec(t, p["kernel"], p["eps"], Lb, Ub, **kw)               # workspace
+    torch.cuda.synchronize()
+    rbf.profile(t, True)
+    e0.record()
+    rbf.fmm_matvec(t, p["kernel"], p["eps"], Lb, Ub, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    msb = e0.elapsed_time(e1)
+    prof = rbf.profile_read(t)
+    rbf.profile(t, False)
+    rbf.check_device_waits()
+    us = torch.empty_like(ld)
+    diffs = []
+    for c in (0, nrhs - 1):
+        rbf.fmm_matvec(t, p["kernel"], p["eps"], Lb[c], us, **kw)
+        torch.cuda.synchronize()
+        diffs.append(float((Ub[c] - us).norm() / us.norm()))
+    nmode = (M // 2 + 1) * (M + 1) ** 4
+    peaks = _peaks()
+    tf32_peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+    cmacs = float(N) * nmode * nrhs                   # useful complex MACs of P2M (and of L2P)
+    passes = {k: v["ms"] for k, v in prof.items() if v["launches"]}
+    tc = {}
+    for name in ("p2m", "l2p"):
+        if name in passes:
+            sec = passes[name] / 1e3
+            tc[name] = {"ms": passes[name],
+                        "fp32_equiv_tflops": 8.0 * cmacs / sec / 1e12,
+                        "tf32_issued_tflops": 24.0 * cmacs / sec / 1e12,
+                        "tf32_peak_tflops": tf32_peak,
+                        "frac_of_tf32_peak": 24.0 * cmacs / sec / 1e12 / tf32_peak}
+    t.free()
+    return {"workload": f"5D N={N} uniform, Gaussian eps=1.5, depth 2, L=4, M={M} "
+                        f"(far-kernel error {err_k:.2e}), {nrhs} columns",
+            "single_column_ms": ms1, "single_column_points_per_s": N / (ms1 / 1e3),
+            "single_column_rel_err_vs_direct_2048": err1,
+            "block_ms": msb, "block_points_x_rhs_per_s": N * nrhs / (msb / 1e3),
+            "speedup_vs_columns": ms1 * nrhs / msb,
+            "block_vs_single_rel_diff": max(diffs), "block_passes_ms": passes,
+            "tensor_core_passes": tc,
+            "tf32_peak_source": "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16 ratio)"}
+
+
 def _oracle_sample(X, lam, p):
     """Centres of the level-1 box at the origin (about N/8), same tree and parameters."""
     k = np.floor(X * 2).astype(np.int64)
@@ -456,6 +538,8 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override the number of centres (profiling)")
     ap.add_argument("--batch", type=int, default=1, help="also time the 256-problem batch")
     ap.add_argument("--solve", type=int, default=1, help="also run the solve comparison")
+    ap.add_argument("--mrhs", type=int, default=1,
+                    help="also time the 5D 16-column product on the tensor cores")
     args = ap.parse_args()
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

@@ -21,12 +21,42 @@
 
 #include "rbf_internal.cuh"
 
-// tuning knobs of the FP32 P2M/L2P tiles (point-loop unroll, resident CTAs per SM)
+// tuning knobs of the FP32 P2M/L2P tiles: point-loop unroll, resident CTAs per
+// SM, rows per thread, column groups, largest block
 #ifndef RBF_FAR_UNROLL
 #define RBF_FAR_UNROLL 1
 #endif
 #ifndef RBF_FAR_MINB
-#define RBF_FAR_MINB 3
+#define RBF_FAR_MINB 4
+#endif
+#ifndef RBF_FAR_RPT
+#define RBF_FAR_RPT 1
+#endif
+#ifndef RBF_FAR_NH
+#define RBF_FAR_NH 2
+#endif
+#ifndef RBF_FAR_BMAX
+#define RBF_FAR_BMAX 256
+#endif
+#ifndef RBF_L2P_MINB
+#define RBF_L2P_MINB RBF_FAR_MINB
+#endif
+#ifndef RBF_L2P_RPT
+#define RBF_L2P_RPT RBF_FAR_RPT
+#endif
+#ifndef RBF_L2P_NH
+#define RBF_L2P_NH RBF_FAR_NH
+#endif
+#ifndef RBF_L2P_BMAX
+#define RBF_L2P_BMAX RBF_FAR_BMAX
+#endif
+// L2P partial sums: 1 = one shared-memory slot per thread and point, reduced
+// once per chunk; 0 = warp shuffles per point
+#ifndef RBF_L2P_SMEMRED
+#define RBF_L2P_SMEMRED 1
+#endif
+#ifndef RBF_L2P_PCH
+#define RBF_L2P_PCH 32
 #endif
 
 namespace {
@@ -177,7 +207,7 @@ __device__ __forceinline__ void tile_coords(int &g, int &h, int &G)
 }
 
 template <typename R, int NCE, int RPT, int NH>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? 192 : 256, sizeof(R) == 4 ? RBF_FAR_MINB : 1) k_p2m(FarArgs<R> a)
+__global__ void __launch_bounds__(sizeof(R) == 4 ? RBF_FAR_BMAX : 256, sizeof(R) == 4 ? RBF_FAR_MINB : 1) k_p2m(FarArgs<R> a)
 {
     using C = cplx<R>;
     constexpr int NCH = NCE / NH;
@@ -251,7 +281,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 192 : 256, sizeof(R) == 4 ? R
 
 // ------------------------------------------------------------------ L2P ---
 template <typename R, int NCE, int RPT, int NH>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? 192 : 256, sizeof(R) == 4 ? RBF_FAR_MINB : 1) k_l2p(FarArgs<R> a)
+__global__ void __launch_bounds__(sizeof(R) == 4 ? RBF_L2P_BMAX : 256, sizeof(R) == 4 ? RBF_L2P_MINB : 1) k_l2p(FarArgs<R> a)
 {
     using C = cplx<R>;
     constexpr int NCH = NCE / NH;
@@ -260,7 +290,8 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 192 : 256, sizeof(R) == 4 ? R
     const int rowlen = seg0 + (a.d - 1) * seg;
     const int boff = a.d == 1 ? 0 : seg0 + (a.d - 2) * seg;
     C *E = reinterpret_cast<C *>(smem_raw);
-    R *part = reinterpret_cast<R *>(E + (size_t)a.pch * rowlen);  // [nwarp][pch]
+    // partial sums: [pch][blockDim] (per thread) or [nwarp][pch] (per warp)
+    R *part = reinterpret_cast<R *>(E + (size_t)a.pch * rowlen);
     const int nwarp = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int g, h, G;
     tile_coords<NH>(g, h, G);
@@ -274,7 +305,8 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 192 : 256, sizeof(R) == 4 ? R
         const int cnt = min(a.pch, np - ch0);
         __syncthreads();
         fill_tables<R>(a, p0 + ch0, cnt, c, (R)1, false, E);
-        for (int q = threadIdx.x; q < nwarp * a.pch; q += blockDim.x) part[q] = (R)0;
+        const int npart = RBF_L2P_SMEMRED ? a.pch * (int)blockDim.x : nwarp * a.pch;
+        for (int q = threadIdx.x; q < npart; q += blockDim.x) part[q] = (R)0;
         __syncthreads();
         for (int row0 = 0; row0 < a.nrow; row0 += RPT * G) {
             RowOff ro[RPT];
@@ -295,18 +327,27 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 192 : 256, sizeof(R) == 4 ? R
             for (int p = 0; p < cnt; ++p) {
                 const C *Ep = E + p * rowlen;
                 const C *B = Ep + boff + h * NCH;
-                C P[RPT];
+                // four partial sums per row keep the FMA chains short
+                C P4[RPT][4];
 #pragma unroll
-                for (int r = 0; r < RPT; ++r) P[r].x = P[r].y = (R)0;
+                for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) P4[r][k].x = P4[r][k].y = (R)0;
 #pragma unroll
                 for (int q = 0; q < NCH; q += 2) {
                     C b0, b1;
                     ld2(B + q, b0, b1);
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
-                        cmac(P[r], Lr[r][q], b0);
-                        cmac(P[r], Lr[r][q + 1], b1);
+                        cmac(P4[r][(q >> 1) & 3], Lr[r][q], b0);
+                        cmac(P4[r][(q >> 1) & 3], Lr[r][q + 1], b1);
                     }
+                }
+                C P[RPT];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    P[r].x = (P4[r][0].x + P4[r][1].x) + (P4[r][2].x + P4[r][3].x);
+                    P[r].y = (P4[r][0].y + P4[r][1].y) + (P4[r][2].y + P4[r][3].y);
                 }
                 R v = (R)0;
 #pragma unroll
@@ -318,21 +359,109 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 192 : 256, sizeof(R) == 4 ? R
                         v += A.x * P[r].x - A.y * P[r].y;
                     }
                 }
+                if (RBF_L2P_SMEMRED) {
+                    part[p * blockDim.x + threadIdx.x] += v;
+                } else {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) part[warp * a.pch + p] += v;
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) part[warp * a.pch + p] += v;
+                }
             }
         }
         __syncthreads();
         for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
             R sum = (R)0;
-            for (int w = 0; w < nwarp; ++w) sum += part[w * a.pch + p];
+            if (RBF_L2P_SMEMRED) {
+                // four interleaved partial sums, added in a fixed order
+                const R *q = part + (size_t)p * blockDim.x;
+                R s4[4] = {(R)0, (R)0, (R)0, (R)0};
+                for (int t = 0; t < (int)blockDim.x; t += 4)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) s4[k] += q[t + k];
+                sum = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+            } else {
+                for (int w = 0; w < nwarp; ++w) sum += part[w * a.pch + p];
+            }
             a.u[p0 + ch0 + p] = sum;
         }
     }
 }
 
 // ------------------------------------------------------------------ M2M ---
+// M2M for d <= 3, two consecutive modes per thread: every child value of the
+// pair is loaded (one 16-byte load in FP32) before any arithmetic, so the
+// 2^d loads of a thread are in flight together.
+template <typename R, int DIM>
+__global__ void __launch_bounds__(256) k_m2m_pair(int M, int n1, int nmode, int64_t ms,
+                                                  const cplx<R> *sh, const int32_t *child_off,
+                                                  const uint64_t *child_key, const cplx<R> *Vc,
+                                                  cplx<R> *Vp)
+{
+    using C = cplx<R>;
+    constexpr int NC = 1 << DIM;
+    const int m = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
+    if (m >= nmode) return;
+    const bool two = m + 1 < nmode;
+    const int p = blockIdx.x;
+    const int c0 = child_off[p], nc = child_off[p + 1] - c0;
+    C v[NC][2];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        if (j < nc) {
+            const C *src = Vc + (int64_t)(c0 + j) * ms + m;
+            if (sizeof(R) == 4 && two) {
+                const float4 w = *reinterpret_cast<const float4 *>(src);
+                v[j][0].x = w.x;
+                v[j][0].y = w.y;
+                v[j][1].x = w.z;
+                v[j][1].y = w.w;
+            } else {
+                v[j][0] = src[0];
+                v[j][1] = two ? src[1] : C{(R)0, (R)0};
+            }
+        }
+    }
+    unsigned bits[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) bits[j] = j < nc ? (unsigned)(child_key[c0 + j] & (NC - 1)) : 0u;
+    C out[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        // per-dimension half shift e^{-i xi_k wc/2} of mode m + e
+        C P[DIM];
+        int r = m + e;
+#pragma unroll
+        for (int t = DIM - 1; t >= 0; --t) {
+            int kidx;
+            if (t > 0) {
+                kidx = r % n1;
+                r /= n1;
+            } else {
+                kidx = r + M / 2;
+            }
+            P[t] = sh[min(kidx, n1 - 1)];
+        }
+        C acc{(R)0, (R)0};
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            if (j < nc) {
+                C ph = (bits[j] & 1u) ? P[0] : cconj(P[0]);
+#pragma unroll
+                for (int t = 1; t < DIM; ++t) ph = cmul(ph, ((bits[j] >> t) & 1u) ? P[t] : cconj(P[t]));
+                cmac(acc, ph, v[j][e]);
+            }
+        }
+        out[e] = acc;
+    }
+    C *dst = Vp + (int64_t)p * ms + m;
+    if (sizeof(R) == 4 && two) {
+        *reinterpret_cast<float4 *>(dst) = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
+    } else {
+        dst[0] = out[0];
+        if (two) dst[1] = out[1];
+    }
+}
+
 // Parents at level l from their children at level l+1 (child width wc).
 template <typename R>
 __global__ void k_m2m(int d, int M, int n1, int nmode, int64_t ms, const cplx<R> *sh,
@@ -712,9 +841,9 @@ __global__ void __launch_bounds__(256) k_m2l_full(int d, int M, int n1, int64_t 
 // block size: multiple of 32*NH threads, fewest idle row slots
 inline int pick_block(int nrow, int rpt, int nh, int bmax)
 {
-    int best = 64, best_waste = 1 << 30;
-    for (int bd = 64; bd <= bmax; bd += 32 * nh) {
-        if (bd % (32 * nh)) continue;
+    const int step = 32 * nh, first = step * ((64 + step - 1) / step);
+    int best = first, best_waste = 1 << 30;
+    for (int bd = first; bd <= bmax; bd += step) {
         const int per = (bd / nh) * rpt;
         const int passes = (nrow + per - 1) / per;
         const int waste = passes * per - nrow;
@@ -729,23 +858,27 @@ inline int pick_block(int nrow, int rpt, int nh, int bmax)
 template <typename R, int NCE>
 int launch_p2m_l2p(bool l2p, const FarArgs<R> &a0, int nleaf, cudaStream_t s)
 {
-    constexpr int RPT = sizeof(R) == 4 ? 2 : 1;
-    constexpr int NH = sizeof(R) == 4 ? 2 : 1;
-    static_assert(NCE % (2 * NH) == 0, "column halves must be even");
+    constexpr int RPT = sizeof(R) == 4 ? RBF_FAR_RPT : 1;
+    constexpr int NH = sizeof(R) == 4 ? (NCE % (2 * RBF_FAR_NH) == 0 ? RBF_FAR_NH : 2) : 1;
+    constexpr int LRPT = sizeof(R) == 4 ? RBF_L2P_RPT : 1;
+    constexpr int LNH = sizeof(R) == 4 ? (NCE % (2 * RBF_L2P_NH) == 0 ? RBF_L2P_NH : 2) : 1;
+    static_assert(NCE % (2 * NH) == 0 && NCE % (2 * LNH) == 0, "column groups must be even");
     // the column segment is read NCE entries wide; all segments of dims >= 1
     // share its length, and dim 0 is the column segment when d == 1
     FarArgs<R> a = a0;
     a.seg = NCE;
     a.seg0 = a.d == 1 ? NCE : even_up(a.n0);
     const int rowlen = a.seg0 + (a.d - 1) * a.seg;
-    a.pch = (int)std::max<int64_t>(1, std::min<int64_t>(64, (64 * 1024) / ((int64_t)rowlen * sizeof(cplx<R>))));
-    const int bd = pick_block(a.nrow, RPT, NH, sizeof(R) == 4 ? 192 : 256);
+    a.pch = (int)std::max<int64_t>(1, std::min<int64_t>(l2p && RBF_L2P_SMEMRED ? RBF_L2P_PCH : 64,
+                                                        (64 * 1024) / ((int64_t)rowlen * sizeof(cplx<R>))));
+    const int bd = l2p ? pick_block(a.nrow, LRPT, LNH, sizeof(R) == 4 ? RBF_L2P_BMAX : 256)
+                       : pick_block(a.nrow, RPT, NH, sizeof(R) == 4 ? RBF_FAR_BMAX : 256);
     size_t smem = (size_t)a.pch * rowlen * sizeof(cplx<R>);
-    if (l2p) smem += (size_t)(bd / 32) * a.pch * sizeof(R);
+    if (l2p) smem += (size_t)(RBF_L2P_SMEMRED ? bd : bd / 32) * a.pch * sizeof(R);
     if (l2p) {
-        RBF_CUDA_TRY(cudaFuncSetAttribute(k_l2p<R, NCE, RPT, NH>,
+        RBF_CUDA_TRY(cudaFuncSetAttribute(k_l2p<R, NCE, LRPT, LNH>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_l2p<R, NCE, RPT, NH><<<nleaf, bd, smem, s>>>(a);
+        k_l2p<R, NCE, LRPT, LNH><<<nleaf, bd, smem, s>>>(a);
     } else {
         RBF_CUDA_TRY(cudaFuncSetAttribute(k_p2m<R, NCE, RPT, NH>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -781,12 +914,26 @@ int rbf_run_m2m(rbf_tree *t, const rbf_plan *p, const cplx<R> *VD, cudaStream_t 
     const int mchunks = ceil_div(p->nmode, mb);
     RBF_REQUIRE(mchunks < 65536, "expansion too large (%lld modes)", (long long)p->nmode);
     rbf_pass_timer tm(t, RBF_PASS_M2M, s, D);
+    const int pchunks = ceil_div(p->nmode, 2 * mb);
     for (int l = D - 1; l >= 0; --l) {
-        dim3 grid(t->lev[l].nbox, mchunks);
         const C *child = l + 1 == D ? VD : (const C *)p->V[l + 1];
-        k_m2m<R><<<grid, mb, 0, s>>>(d, p->M, p->n1, (int)p->nmode, p->mstride,
-                                     (const C *)p->shift_ph + (int64_t)(l + 1) * p->n1,
-                                     t->lev[l].child_off, t->lev[l + 1].key, child, (C *)p->V[l]);
+        const C *sh = (const C *)p->shift_ph + (int64_t)(l + 1) * p->n1;
+        if (d <= 3) {
+            dim3 grid(t->lev[l].nbox, pchunks);
+#define RBF_M2M_PAIR(DD)                                                                          \
+    k_m2m_pair<R, DD><<<grid, mb, 0, s>>>(p->M, p->n1, (int)p->nmode, p->mstride, sh,              \
+                                          t->lev[l].child_off, t->lev[l + 1].key, child,           \
+                                          (C *)p->V[l])
+            if (d == 1) RBF_M2M_PAIR(1);
+            else if (d == 2) RBF_M2M_PAIR(2);
+            else RBF_M2M_PAIR(3);
+#undef RBF_M2M_PAIR
+        } else {
+            dim3 grid(t->lev[l].nbox, mchunks);
+            k_m2m<R><<<grid, mb, 0, s>>>(d, p->M, p->n1, (int)p->nmode, p->mstride, sh,
+                                         t->lev[l].child_off, t->lev[l + 1].key, child,
+                                         (C *)p->V[l]);
+        }
         RBF_LAUNCH_CHECK();
     }
     return RBF_OK;
