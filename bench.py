@@ -260,7 +260,8 @@ def run_ours(args):
                "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f32", "data": "synthetic (seeded uniform centres, N(0,1) coefficients)",
-               "config": {"workload": "3D N=2^20 uniform, IMQ eps=2, depth 5, M=32, L=4, alpha=4.5",
+               "config": {"workload": "3D N=%s uniform, IMQ eps=2, depth %d, M=%d, L=4, alpha=4.5"
+                                      % ("2^20" if N == 1 << 20 else str(N), info["depth"], p["M"]),
                           "N": N, "d": 3, "depth": info["depth"], "M": p["M"], "modes_per_leaf":
                           nmode, "n_leaf": nleaf, "near_pairs": pairs,
                           "parallelism": "replicas" if world > 1 else "single GPU",
@@ -274,7 +275,8 @@ def run_ours(args):
         if args.solve:
             out["solve"] = solve_measurement(rbf, dev)
         if args.mrhs:
-            out["multi_rhs"] = multi_rhs_measurement(rbf, dev)
+            out["multi_rhs"] = multi_rhs_measurement(rbf, dev, nrhs=args.mrhs_cols, n=args.mrhs_n,
+                                                     M=args.mrhs_M)
         if not args.skip_cpu and world == 1:
             out["cpu_baseline"] = cpu_baseline(X, lam, p, budget_s=args.cpu_budget)
     if dist:
@@ -400,7 +402,7 @@ def solve_measurement(rbf, dev):
     return res
 
 
-def multi_rhs_measurement(rbf, dev, tol=1.5e-7, nrhs=16):
+def multi_rhs_measurement(rbf, dev, tol=1.5e-7, nrhs=16, n=1 << 19, M=0):
     """d = 5, N = 2^19 uniform, Gaussian eps = 1.5, depth 2 (512 points per leaf), L = 4,
     M = the smallest even M whose measured far-kernel error is <= 1.5e-7.  Times one FP32
     product of a single column and one of the 16-column block (P2M and L2P of the block on
@@ -409,12 +411,15 @@ def multi_rhs_measurement(rbf, dev, tol=1.5e-7, nrhs=16):
     import torch
     import workloads
     from paper_1606_07652_gb300 import _lib
-    X, lam, lamb, targets, p = workloads.config5(nrhs=nrhs)
+    X, lam, lamb, targets, p = workloads.config5(n=n, nrhs=nrhs)
     N = len(X)
-    M = 8
-    err_k = _lib.kernel_error(p["kernel"], p["eps"], 5, M, p["L"], 0.0, 1.0, p["depth"])
-    while err_k > tol and M < 24:
-        M += 2
+    if M <= 0:   # grow M to the error target
+        M = 8
+        err_k = _lib.kernel_error(p["kernel"], p["eps"], 5, M, p["L"], 0.0, 1.0, p["depth"])
+        while err_k > tol and M < 24:
+            M += 2
+            err_k = _lib.kernel_error(p["kernel"], p["eps"], 5, M, p["L"], 0.0, 1.0, p["depth"])
+    else:
         err_k = _lib.kernel_error(p["kernel"], p["eps"], 5, M, p["L"], 0.0, 1.0, p["depth"])
     Xd = torch.as_tensor(X, device=dev)
     t = rbf.tree_build(Xd, lo=np.zeros(5), side=1.0, depth=p["depth"])
@@ -540,6 +545,9 @@ def main():
     ap.add_argument("--solve", type=int, default=1, help="also run the solve comparison")
     ap.add_argument("--mrhs", type=int, default=1,
                     help="also time the 5D 16-column product on the tensor cores")
+    ap.add_argument("--mrhs-n", type=int, default=1 << 19, help="centres of the 5D product")
+    ap.add_argument("--mrhs-M", type=int, default=0, help="modes per dimension (0: error target)")
+    ap.add_argument("--mrhs-cols", type=int, default=16, help="columns of the 5D block")
     args = ap.parse_args()
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

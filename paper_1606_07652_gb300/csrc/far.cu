@@ -757,15 +757,16 @@ __global__ void __launch_bounds__(256) k_m2l_full(int d, int M, int n1, int64_t 
                                                   const cplx<R> *VD, cplx<R> *Lx)
 {
     using C = cplx<R>;
+    constexpr int SB = S == 4 ? 2 : (S == 8 ? 3 : 4);   // bits per coordinate
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *grid = reinterpret_cast<C *>(smem_raw);              // [nbox][MC]
-    int *kid = reinterpret_cast<int *>(grid + 0);            // placeholder, set below
     int nbox = 1;
     for (int t = 0; t < d; ++t) nbox *= S;
-    kid = reinterpret_cast<int *>(grid + (int64_t)nbox * MC);  // [d][MC] frequency index
+    C *grid = reinterpret_cast<C *>(smem_raw);                          // [nbox][MC]
+    int *kid = reinterpret_cast<int *>(grid + (int64_t)nbox * MC);      // [d][MC] frequency index
+    uint32_t *lc = reinterpret_cast<uint32_t *>(kid + d * MC);          // [nleaf] packed coordinates
     const int64_t m0 = (int64_t)blockIdx.x * MC;
     const int mc = (int)min((int64_t)MC, nmode - m0);
-    const int D = __ffs(S) - 1;
+    const int D = SB;
     for (int q = threadIdx.x; q < d * MC; q += blockDim.x) {
         const int t = q / MC, mm = q - t * MC;
         int64_t r = m0 + min(mm, mc - 1);
@@ -782,16 +783,21 @@ __global__ void __launch_bounds__(256) k_m2l_full(int d, int M, int n1, int64_t 
         }
         kid[q] = k;
     }
+    // leaf coordinates k_t (SB bits each, dimension 0 lowest); grid index = the same
+    // bits read as one integer
+    for (int l = threadIdx.x; l < nleaf; l += blockDim.x) {
+        int k[RBF_MAX_DIM];
+        decode_key(leaf_key[l], d, D, k);
+        uint32_t w = 0;
+        for (int t = d - 1; t >= 0; --t) w = (w << SB) | (uint32_t)k[t];
+        lc[l] = w;
+    }
     for (int q = threadIdx.x; q < nbox * MC; q += blockDim.x) grid[q] = C{(R)0, (R)0};
     __syncthreads();
     for (int q = threadIdx.x; q < nleaf * MC; q += blockDim.x) {
         const int l = q / MC, mm = q - l * MC;
         if (mm >= mc) continue;
-        int k[RBF_MAX_DIM];
-        decode_key(leaf_key[l], d, D, k);
-        int g = 0;
-        for (int t = d - 1; t >= 0; --t) g = g * S + k[t];
-        grid[g * MC + mm] = VD[(int64_t)l * ms + m0 + mm];
+        grid[(int64_t)lc[l] * MC + mm] = VD[(int64_t)l * ms + m0 + mm];
     }
     __syncthreads();
     int stride = 1;
@@ -821,19 +827,19 @@ __global__ void __launch_bounds__(256) k_m2l_full(int d, int M, int n1, int64_t 
     for (int q = threadIdx.x; q < nleaf * MC; q += blockDim.x) {
         const int l = q / MC, mm = q - l * MC;
         if (mm >= mc) continue;
-        int k[RBF_MAX_DIM];
-        decode_key(leaf_key[l], d, D, k);
-        int g = 0;
-        for (int t = d - 1; t >= 0; --t) g = g * S + k[t];
+        const uint32_t w = lc[l];
         const int64_t m = m0 + mm;
-        C ph = root_ph[(int64_t)k[0] * n1 + kid[mm]];
-        for (int t = 1; t < d; ++t) ph = cmul(ph, root_ph[((int64_t)t * S + k[t]) * n1 + kid[t * MC + mm]]);
+        C ph = root_ph[(int64_t)(w & (S - 1)) * n1 + kid[mm]];
+        for (int t = 1; t < d; ++t) {
+            const int kt = (int)((w >> (SB * t)) & (S - 1));
+            ph = cmul(ph, root_ph[((int64_t)t * S + kt) * n1 + kid[t * MC + mm]]);
+        }
         const C r = cmul(ph, V0[m]);
-        const C sa = grid[g * MC + mm];
-        const R w = omegaC[m];
+        const C sa = grid[(int64_t)w * MC + mm];
+        const R wC = omegaC[m];
         C out;
-        out.x = w * (r.x - sa.x);
-        out.y = w * (r.y - sa.y);
+        out.x = wC * (r.x - sa.x);
+        out.y = wC * (r.y - sa.y);
         Lx[(int64_t)l * ms + m] = out;
     }
 }
@@ -966,7 +972,8 @@ int rbf_run_m2l(rbf_tree *t, const rbf_plan *p, const cplx<R> *VD, cplx<R> *L, c
         const int S = 1 << D;
         const int64_t nbox = (int64_t)1 << (d * D);
         const int MC = (int)std::max<int64_t>(1, std::min<int64_t>(16, (96 * 1024) / (nbox * (int64_t)sizeof(C))));
-        const size_t smem = (size_t)nbox * MC * sizeof(C) + (size_t)d * MC * sizeof(int);
+        const size_t smem = (size_t)nbox * MC * sizeof(C) + (size_t)d * MC * sizeof(int) +
+                            (size_t)t->nleaf() * sizeof(uint32_t);
         const int nblk = ceil_div(p->nmode, MC);
 #define RBF_M2L_FULL(SS)                                                                          \
     do {                                                                                          \

@@ -23,20 +23,21 @@
 // hi*hi + hi*lo + lo*hi (three-term split TF32, FP32-level accuracy).
 //
 // Tile: 128 rows (TMEM lanes) x 2*NT real columns (NT complex: 16, 32, 48 or
-// 64), K staged 8 points (rows) = 48 TF32 values at a time in two
-// shared-memory stages; one thread issues the six MMAs of a stage and commits
-// them to the stage's mbarrier, all 256 threads generate the next stage
-// meanwhile.  Accumulation runs in blocks of two stages per TMEM buffer, each
-// block folded into FP32 registers (see tc_pipeline).  Operands are K-major
-// without swizzle: 8-row x 16-byte core matrices, 128 B apart along K and
-// 1536 B apart along rows.  P2M keeps the leaf's points and coefficients in
-// shared memory; L2P streams the rows of the local expansions through a ring
-// of shared-memory slots filled by bulk asynchronous copies (TMA).
-//
-// Every wait on an mbarrier is bounded; a wait that gives up sets a status bit
-// (read by rbf_tc_fetch_status), the kernel skips its remaining work, waits
-// once more (bounded) for its MMAs in flight, frees its tensor memory and
-// returns.
+// 64); K advances 8 points (mode rows) = 48 TF32 values per stage.  Operands
+// are K-major without swizzle: 8-row x 16-byte core matrices, 128 B apart
+// along K and 1536 B apart along rows.  The CTA is split by warp roles:
+//   producers (8 warps)  build the operands of a ring of stages,
+//   MMA (1 warp)         one lane issues the six MMAs of a stage, commits them
+//                        to the stage's "empty" barrier and, at the end of an
+//                        accumulation block, to the block's "full" barrier,
+//   epilogue (8 warps)   add each finished block into FP32 registers,
+//   copy (1 warp, L2P)   streams the mode rows of the local expansions into a
+//                        ring of shared-memory slots with bulk copies (TMA).
+// Roles meet only at mbarriers; every wait on one is bounded.  A wait that
+// gives up sets a status bit (read by rbf_tc_fetch_status) and a shared abort
+// flag; the roles then skip their remaining work (producers still pass their
+// named barriers), the MMA lane waits once more (bounded) for its last
+// commit, tensor memory is freed and the kernel returns.
 #include <algorithm>
 
 #include "rbf_internal.cuh"
@@ -111,19 +112,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
         : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
-}
-
-// bounded wait for the completion of phase `parity`; false when it gave up
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
-            atomicOr(&g_tc_status, 1u);
-            return false;
-        }
-    }
-    return true;
 }
 
 __device__ __forceinline__ void tc_fence_before()
@@ -252,57 +240,21 @@ __device__ __forceinline__ void decode_key(uint64_t key, int d, int l, int *k)
         for (int t = 0; t < d; ++t) k[t] |= (int)((key >> (b * d + t)) & 1u) << b;
 }
 
-// Table offsets of the row factors of mode row `row`: o[0] = k0 (dimension-0
-// segment), o[t] = n0 + (t-1) n1 + k_t for t = 1 .. d-2.
-struct RowFac {
-    int o[RBF_MAX_DIM - 1];
-};
-__device__ __forceinline__ RowFac row_factors(int row, int d, int n0, int n1)
+// prod_{t<d-2} E_t[k_t] of the prefix Q = (k0, .., k_{d-3}) of a mode row (d >= 3)
+__device__ __forceinline__ float2 prefix_phase(const float2 *E, int Q, int d, int n0, int n1)
 {
-    RowFac f;
-#pragma unroll
-    for (int t = 0; t < RBF_MAX_DIM - 1; ++t) f.o[t] = 0;
-#pragma unroll
-    for (int t = RBF_MAX_DIM - 2; t >= 1; --t) {
-        if (t <= d - 2) {
-            f.o[t] = n0 + (t - 1) * n1 + row % n1;
-            row /= n1;
-        }
+    float2 v = make_float2(1.0f, 0.0f);
+    for (int t = d - 3; t >= 1; --t) {
+        v = cmul(v, E[n0 + (t - 1) * n1 + Q % n1]);
+        Q /= n1;
     }
-    f.o[0] = row;
-    return f;
-}
-
-// prod_{t<d-1} E[o_t]  (1 when d == 1)
-__device__ __forceinline__ float2 row_phase(const float2 *E, const RowFac &f, int d)
-{
-    if (d == 1) return make_float2(1.0f, 0.0f);
-    float2 a = E[f.o[0]];
-#pragma unroll
-    for (int t = 1; t < RBF_MAX_DIM - 1; ++t)
-        if (t < d - 1) a = cmul(a, E[f.o[t]]);
-    return a;
-}
-
-// next mode row: the fastest digit k_{d-2} first, carries towards k0
-__device__ __forceinline__ void row_next(RowFac &f, int d, int n0, int n1)
-{
-#pragma unroll
-    for (int t = RBF_MAX_DIM - 2; t >= 1; --t) {
-        if (t <= d - 2) {
-            const int base = n0 + (t - 1) * n1;
-            if (++f.o[t] < base + n1) return;
-            f.o[t] = base;
-        }
-    }
-    ++f.o[0];
+    return cmul(v, E[Q]);
 }
 
 struct TcArgs {
     int d, M, D, n0, n1, nrow, ncol, G;
     int NT;                  // complex columns of the tile (16, 32, 48 or 64)
     int rowlen, rowpad;      // per-point table length, padded row stride (odd)
-    int lcap;                // points of the largest leaf (P2M staging)
     uint32_t idesc, tcols;   // instruction descriptor, allocated TMEM columns
     int64_t mstride, N, vstride;
     double lo[RBF_MAX_DIM];
@@ -344,123 +296,105 @@ __device__ __forceinline__ void leaf_centre(const TcArgs &a, int leaf, double *c
     for (int t = 0; t < a.d; ++t) c[t] = a.lo[t] + ((double)k[t] + 0.5) * w;
 }
 
-// the two operand stages at the start of dynamic shared memory
-struct StageLayout {
-    unsigned char *stage[2];
-    uint32_t wbytes;
-};
-__device__ __forceinline__ StageLayout stages(unsigned char *smem, int NT)
-{
-    StageLayout s;
-    s.wbytes = (uint32_t)(2 * NT) * kKStage * 4;
-    s.stage[0] = smem;
-    s.stage[1] = smem + kABytes + s.wbytes;
-    return s;
-}
+// ---------------------------------------------------------- warp roles ----
+constexpr int kProdWarps = 8;                          // warps 0..7: operand producers
+constexpr int kMmaWarp = kProdWarps;                   // warp 8: MMA issue (one lane)
+constexpr int kEpiWarp0 = kProdWarps + 1;              // warps 9..16: accumulator epilogue
+constexpr int kEpiWarps = 8;
+constexpr int kCopyWarp = kEpiWarp0 + kEpiWarps;       // warp 17: bulk copies
+constexpr int kTcThreads = 32 * (kCopyWarp + 1);       // 576
+constexpr int kP2MStages = 3, kL2PStages = 2, kMaxStages = 3;
+constexpr int kRing = 8;                               // copy-slot barriers
+constexpr int kRingE = 8, kRingL = 4;                  // copy slots of P2M, L2P
+constexpr int kBarProd = 1, kBarEpi = 2;               // named barriers (0 = __syncthreads)
+constexpr int kPF = 48;   // prefixes per 128-row tile: 128 / n1 + 2 <= 48 for n1 >= 3
 
-// Accumulation blocks: the MMAs of kBlock consecutive stages accumulate into
-// one of two TMEM buffers (columns [buf * 2NT, buf * 2NT + 2NT)), starting from
-// zero; a finished block is added into FP32 registers with round-to-nearest
-// adds.  The tensor core's own accumulation rounds towards zero, so a long
-// chain of MMAs into one accumulator shrinks it by about one ulp per MMA; short
-// blocks keep that below 1e-6 relative.
+// Accumulation blocks: the MMAs of kBlock consecutive stages of a work item
+// accumulate into one of two TMEM buffers (columns [buf * 2NT, buf * 2NT + 2NT)),
+// starting from zero; the epilogue adds a finished block into FP32 registers
+// with round-to-nearest adds.  The tensor core's own accumulation rounds
+// towards zero, so a long chain of MMAs into one accumulator shrinks it by
+// about one ulp per MMA; short blocks keep that below 1e-6 relative.
 constexpr int kBlock = 2;
 __host__ __device__ __forceinline__ bool block_end(int ch, int nch)
 {
     return (ch + 1) % kBlock == 0 || ch == nch - 1;
 }
-__device__ __forceinline__ int block_buf(int ch) { return (ch / kBlock) & 1; }
 
-// Runs the stage pipeline over nch stages.  gen(ch, tile) writes the operands
-// of stage ch and returns false when one of its waits gave up; post(ch) runs
-// on all threads once every thread has finished gen(ch); flush(col0) adds the
-// finished TMEM block at column col0 into registers (all warps, converged).
-// Returns false when a wait gave up.
-template <class Gen, class Post, class Flush>
-__device__ __forceinline__ bool tc_pipeline(int nch, const StageLayout &SL, uint32_t tmem,
-                                            uint32_t idesc, int NT, uint64_t *bar, Gen &&gen,
-                                            Post &&post, Flush &&flush)
+struct Sync {
+    uint64_t *full, *empty;   // [kMaxStages] producers -> MMA, MMA -> producers
+    uint64_t *accf, *acce;    // [2] MMA -> epilogue (block done), epilogue -> MMA (drained)
+    uint64_t *rfull, *rempty; // [kRing] copies landed, slot consumed
+    uint32_t *tslot;
+    volatile int *abort;
+};
+constexpr int kSyncBytes = 16 + 8 * (2 * kMaxStages + 4 + 2 * kRing) + 16;
+
+__device__ __forceinline__ Sync sync_at(void *end)
 {
-    const int tid = threadIdx.x;
-    for (int ch = 0; ch < nch; ++ch) {
-        const int st = ch & 1;
-        bool ok = true;
-        // the MMAs of stage ch-2 (and all before) are complete once its commit arrived
-        if (ch >= 2) ok = mbar_wait(smem_u32(&bar[st]), ((ch - 2) >> 1) & 1);
-        if (__syncthreads_or(!ok)) return false;
-        if (ch >= 2 && block_end(ch - 2, nch)) {
-            tc_fence_after();
-            flush((uint32_t)(block_buf(ch - 2) * 2 * NT));
-            tc_fence_before();
-        }
-        unsigned char *tile = SL.stage[st];
-        ok = gen(ch, tile);
-        fence_async_smem();
-        if (__syncthreads_or(!ok)) return false;
-        post(ch);
-        if (tid == 0) {
-            const uint32_t a0 = smem_u32(tile), b0 = a0 + (uint32_t)kABytes;
-            const uint32_t d = tmem + (uint32_t)(block_buf(ch) * 2 * NT);
-            const bool fresh = ch % kBlock == 0;
-            tc_fence_after();
-#pragma unroll
-            for (int s = 0; s < kSlots; ++s)
-                mma_tf32(d, smem_desc(a0 + 256u * s), smem_desc(b0 + 256u * s), idesc,
-                         (fresh && s == 0) ? 0u : 1u);
-            mma_commit(smem_u32(&bar[st]));
+    Sync y;
+    uint64_t *b = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(end) + 15) & ~(uintptr_t)15);
+    y.full = b;
+    y.empty = b + kMaxStages;
+    y.accf = b + 2 * kMaxStages;
+    y.acce = y.accf + 2;
+    y.rfull = y.acce + 2;
+    y.rempty = y.rfull + kRing;
+    y.tslot = reinterpret_cast<uint32_t *>(y.rempty + kRing);
+    y.abort = reinterpret_cast<volatile int *>(y.tslot + 1);
+    return y;
+}
+
+__device__ __forceinline__ void sync_init(const Sync &y)
+{
+    for (int k = 0; k < kMaxStages; ++k) {
+        mbar_init(smem_u32(&y.full[k]), kProdWarps);
+        mbar_init(smem_u32(&y.empty[k]), 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+        mbar_init(smem_u32(&y.accf[k]), 1);
+        mbar_init(smem_u32(&y.acce[k]), kEpiWarps);
+    }
+    for (int k = 0; k < kRing; ++k) {
+        mbar_init(smem_u32(&y.rfull[k]), 1);
+        mbar_init(smem_u32(&y.rempty[k]), kProdWarps);
+    }
+    *y.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void named_bar(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// bounded wait that also gives up once another role has aborted
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort)
+{
+    const uint32_t b = smem_u32(bar);
+    const long long t0 = clock64();
+    while (!mbar_try_wait(b, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            atomicOr(&g_tc_status, 1u);
+            *abort = 1;
+            return false;
         }
     }
-    if (nch == 0) return true;
-    const bool ok = mbar_wait(smem_u32(&bar[(nch - 1) & 1]), ((nch - 1) >> 1) & 1);
-    if (__syncthreads_or(!ok)) return false;
-    tc_fence_after();
-    if (nch >= 2 && block_end(nch - 2, nch)) flush((uint32_t)(block_buf(nch - 2) * 2 * NT));
-    flush((uint32_t)(block_buf(nch - 1) * 2 * NT));
     return true;
 }
 
-// shared-memory barriers (two MMA stages + nring copy slots) and the TMEM slot
-struct CtaSync {
-    uint64_t *bar;    // [2] MMA stages
-    uint64_t *full;   // [nring] copy slots
-    uint32_t *tslot;
-};
-__device__ __forceinline__ CtaSync cta_sync_at(void *end, int nring)
+// bounded wait used while draining after an abort
+__device__ __forceinline__ void wait_bounded(uint64_t *bar, uint32_t parity)
 {
-    CtaSync c;
-    c.bar = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(end) + 15) & ~(uintptr_t)15);
-    c.full = c.bar + 2;
-    c.tslot = reinterpret_cast<uint32_t *>(c.full + nring);
-    return c;
-}
-constexpr int kSyncBytes = 16 + 8 * (2 + 8) + 16;   // alignment, barriers, TMEM slot
-
-__device__ __forceinline__ void cta_setup(const CtaSync &cs, int nring, uint32_t tcols)
-{
-    if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&cs.bar[0]), 1);
-        mbar_init(smem_u32(&cs.bar[1]), 1);
-        for (int k = 0; k < nring; ++k) mbar_init(smem_u32(&cs.full[k]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    if ((threadIdx.x >> 5) == 0) tmem_alloc(smem_u32(cs.tslot), tcols);
-}
-
-// after an abandoned pipeline: bounded wait for the last committed MMA stage
-__device__ __forceinline__ void drain(const CtaSync &cs, int nch)
-{
-    if (threadIdx.x == 0 && nch > 0)
-        (void)mbar_wait(smem_u32(&cs.bar[(nch - 1) & 1]), ((nch - 1) >> 1) & 1);
-}
-
-__device__ __forceinline__ void cta_teardown(uint32_t tmem, uint32_t tcols)
-{
-    tc_fence_before();
-    __syncthreads();
-    if ((threadIdx.x >> 5) == 0) {
-        tc_fence_after();
-        tmem_dealloc(tmem, tcols);
+    const uint32_t b = smem_u32(bar);
+    const long long t0 = clock64();
+    while (!mbar_try_wait(b, parity) && clock64() - t0 < kWaitCycles) {
     }
 }
 
@@ -480,102 +414,54 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
         : "memory");
 }
 
-// ------------------------------------------------------------------ P2M ---
-// grid (leaf, row tile, column tile); V_r[leaf][row * ncol + col].  NT = 16 NTH
-// complex columns; warp w reads TMEM lanes 32 (w & 3) .. and the complex
-// columns [(w >> 2) NT/2, (w >> 2 + 1) NT/2) (real and imaginary parts).  The
-// leaf's coordinates and coefficients are staged in shared memory once.
+// MMA lane, one work item of nch stages: six MMAs per stage into the block's
+// TMEM buffer; commits to the stage's empty barrier and, at a block end, to the
+// block's full barrier.  gc / gb count stages / blocks over all items.
+template <int S>
+__device__ __forceinline__ void mma_item(const Sync &y, int nch, int &gc, int &gb, int &last,
+                                         unsigned char *smem, uint32_t sbytes, uint32_t tmem,
+                                         uint32_t idesc, int NT)
+{
+    for (int lc = 0; lc < nch; ++lc, ++gc) {
+        const int s = gc % S, buf = gb & 1;
+        if (*y.abort) {
+            if (block_end(lc, nch)) ++gb;
+            continue;
+        }
+        if (lc % kBlock == 0 && gb >= 2 && !wait_or_abort(&y.acce[buf], ((gb - 2) >> 1) & 1, y.abort))
+            continue;
+        if (!wait_or_abort(&y.full[s], (gc / S) & 1, y.abort)) continue;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(smem + s * sbytes), b0 = a0 + (uint32_t)kABytes;
+        const uint32_t d = tmem + (uint32_t)(buf * 2 * NT);
+        const bool fresh = lc % kBlock == 0;
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k)
+            mma_tf32(d, smem_desc(a0 + 256u * k), smem_desc(b0 + 256u * k), idesc,
+                     (fresh && k == 0) ? 0u : 1u);
+        mma_commit(smem_u32(&y.empty[s]));
+        if (block_end(lc, nch)) {
+            mma_commit(smem_u32(&y.accf[buf]));
+            ++gb;
+        }
+        last = gc;
+    }
+}
+
+// epilogue warp, one work item: add its blocks into acc_re / acc_im (zeroed here)
 template <int NTH>
-__global__ void __launch_bounds__(kThreads, 1) k_p2m_tc(const TcArgs a)
+__device__ __forceinline__ void epi_item(const Sync &y, int nch, int &gb, uint32_t tlane, int h,
+                                         float *acc_re, float *acc_im)
 {
     constexpr int NT = 16 * NTH, NH = NT / 2;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    const StageLayout SL = stages(smem, NT);
-    unsigned char *tail = smem + 2 * (kABytes + SL.wbytes);
-    float2 *E = reinterpret_cast<float2 *>(tail);                      // [kKS][rowlen]
-    float *xl = reinterpret_cast<float *>(E + kKS * a.rowlen);         // [d][lcap]
-    float *ll = xl + a.d * a.lcap;                                     // [G][lcap]
-    const CtaSync cs = cta_sync_at(ll + a.G * a.lcap, 0);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int leaf = blockIdx.x;
-    const int row0 = blockIdx.y * kRows;
-    const int n0c = blockIdx.z * NT;
-    const int ntot = a.ncol * a.G;
-    const int64_t p0 = a.leaf_off[leaf];
-    const int np = min(a.leaf_off[leaf + 1] - (int)p0, a.lcap);
-    const int nch = (np + kKS - 1) / kKS;
-
-    double c[RBF_MAX_DIM];
-    leaf_centre(a, leaf, c);
-    cta_setup(cs, 0, a.tcols);
-    for (int idx = tid; idx < a.d * np; idx += kThreads) {
-        const int t = idx / np, p = idx - t * np;
-        xl[t * a.lcap + p] = a.xs[(int64_t)t * a.N + p0 + p];
-    }
-    for (int idx = tid; idx < a.G * np; idx += kThreads) {
-        const int r = idx / np, p = idx - r * np;
-        ll[r * a.lcap + p] = a.lam[(int64_t)r * a.N + p0 + p];
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *cs.tslot;
-
-    // A side: this thread's mode row and point quad
-    const int rt = tid & (kRows - 1), qa = tid >> 7;
-    const int row = row0 + rt;
-    const bool row_ok = row < a.nrow;
-    const RowFac rf = row_factors(row_ok ? row : 0, a.d, a.n0, a.n1);
-    const int ocol = a.d == 1 ? 0 : a.n0 + (a.d - 2) * a.n1;
-    // accumulators: lane quarter q, column half h
-    const int q = warp & 3, h = warp >> 2;
-    const uint32_t tlane = tmem + ((uint32_t)(32 * q) << 16);
-    float acc_re[NH], acc_im[NH];
 #pragma unroll
     for (int j = 0; j < NH; ++j) acc_re[j] = acc_im[j] = 0.0f;
-
-    auto gen = [&](int ch, unsigned char *tile) -> bool {
-        const int k0 = ch * kKS;
-        const int cnt = min(kKS, np - k0);
-        for (int idx = tid; idx < kKS * a.rowlen; idx += kThreads) {
-            const int p = idx / a.rowlen, j = idx - p * a.rowlen;
-            E[idx] = p < cnt ? table_entry(a, xl + k0 + p, a.lcap, j, c, -1.0f)
-                             : make_float2(0.0f, 0.0f);
-        }
-        __syncthreads();
-        {
-            float re[4], im[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float2 v = row_ok ? row_phase(E + (4 * qa + e) * a.rowlen, rf, a.d)
-                                        : make_float2(0.0f, 0.0f);
-                re[e] = v.x;
-                im[e] = v.y;
-            }
-            put_a(tile, rt, qa, re, im);
-        }
-        for (int idx = tid; idx < 2 * NT; idx += kThreads) {
-            const int j = idx >> 1, qq = idx & 1;
-            const int n = n0c + j;
-            float wr[4] = {0, 0, 0, 0}, wi[4] = {0, 0, 0, 0};
-            if (n < ntot) {
-                const int r = n / a.ncol, col = n - r * a.ncol;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int p = 4 * qq + e;
-                    const float2 ev = E[p * a.rowlen + ocol + col];
-                    const float l = p < cnt ? ll[r * a.lcap + k0 + p] : 0.0f;
-                    wr[e] = ev.x * l;
-                    wi[e] = ev.y * l;
-                }
-            }
-            put_w(tile + kABytes, j, NT, qq, wr, wi);
-        }
-        return true;
-    };
-    auto post = [&](int) {};
-    auto flush = [&](uint32_t col0) {
+    const int nb = (nch + kBlock - 1) / kBlock;
+    for (int b = 0; b < nb; ++b, ++gb) {
+        const int buf = gb & 1;
+        if (*y.abort || !wait_or_abort(&y.accf[buf], (gb >> 1) & 1, y.abort)) continue;
+        tc_fence_after();
+        const uint32_t col0 = (uint32_t)(buf * 2 * NT);
 #pragma unroll
         for (int g = 0; g < NTH; ++g) {
             float re[8], im[8];
@@ -588,196 +474,407 @@ __global__ void __launch_bounds__(kThreads, 1) k_p2m_tc(const TcArgs a)
                 acc_im[8 * g + e] += im[e];
             }
         }
-    };
-    const bool ok = tc_pipeline(nch, SL, tmem, a.idesc, NT, cs.bar, gen, post, flush);
-    if (ok) {
-        // registers -> shared staging [kRows][NT + 1] -> coalesced stores
-        __syncthreads();
-        float2 *S = reinterpret_cast<float2 *>(smem);
-        const int sst = NT + 1;
-        const int r = 32 * q + lane;
-#pragma unroll
-        for (int j = 0; j < NH; ++j) S[r * sst + h * NH + j] = make_float2(acc_re[j], acc_im[j]);
-        __syncthreads();
-        for (int idx = tid; idx < kRows * NT; idx += kThreads) {
-            const int rr = idx / NT, j = idx - rr * NT;
-            const int n = n0c + j, grow = row0 + rr;
-            if (grow >= a.nrow || n >= ntot) continue;
-            const int rhs = n / a.ncol, col = n - rhs * a.ncol;
-            a.V[(int64_t)rhs * a.vstride + (int64_t)leaf * a.mstride + (int64_t)grow * a.ncol + col] =
-                S[rr * sst + j];
-        }
-    } else {
-        drain(cs, nch);
+        tc_fence_before();
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(smem_u32(&y.acce[buf]));
     }
-    cta_teardown(tmem, a.tcols);
 }
 
-// ------------------------------------------------------------------ L2P ---
-// grid (leaf, point tile, RHS tile); the tile's NT = 16 NTH complex columns hold
-// Rg whole right-hand sides (Rg * ncol <= NT), so every u_{i,r} is finished in
-// the CTA.  Each block of T is contracted with B'_i at once:
-//   S_i[j] += Re(B'_i[col(j)] T_i[j]),  u_{i,r} = sum of S_i over the columns of r.
-// The kKS-row slices of L_r (contiguous: rows are row-major) arrive through a
-// ring of kRing shared-memory slots, kRing stages ahead of their use.
-constexpr int kRing = 6;
-
-template <int NTH>
-__global__ void __launch_bounds__(kThreads, 1) k_l2p_tc(const TcArgs a, int Rg)
+// ---------------------------------------------------------- point tables --
+// E[i][j] = e^{-i xi_k (x_{i,t} - c_t)} of every point i (sorted order) for the
+// table entries j of Eq. (P2M) (dimension-0 segment k0 = 0..M/2, then
+// k = -M/2..M/2 per dimension), rows padded to rowpadE (even) entries; and the
+// coefficients of the group, point-major: Lt[i][r] = lambda_r[i] (gpad columns,
+// a multiple of 4, zero beyond G).
+__global__ void __launch_bounds__(256) k_point_tables(const TcArgs a, int rowpadE, float2 *Eg,
+                                                      int gpad, float *Lt)
 {
-    constexpr int NT = 16 * NTH, NH = NT / 2;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    const StageLayout SL = stages(smem, NT);
-    unsigned char *tail = smem + 2 * (kABytes + SL.wbytes);
-    const int slot_c = Rg * kKS * a.ncol;                              // complex per ring slot
-    float2 *ring = reinterpret_cast<float2 *>(tail);                   // [kRing][Rg][kKS][ncol]
-    float2 *E = ring + kRing * slot_c;                                 // [kRows][rowpad]
-    const CtaSync cs = cta_sync_at(E + kRows * a.rowpad, kRing);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int leaf = blockIdx.x;
     const int64_t p0 = a.leaf_off[leaf];
     const int np = a.leaf_off[leaf + 1] - (int)p0;
-    const int pt0 = blockIdx.y * kRows;
-    if (pt0 >= np) return;   // uniform: before any allocation or barrier
-    const int cnt = min(kRows, np - pt0);
-    const int rg0 = blockIdx.z * Rg;
-    const int rgv = min(Rg, a.G - rg0);   // right-hand sides present in the tile
-    const int ncolt = Rg * a.ncol;        // columns of the tile
-    const int nch = (a.nrow + kKS - 1) / kKS;
-
     double c[RBF_MAX_DIM];
     leaf_centre(a, leaf, c);
-    cta_setup(cs, kRing, a.tcols);
-    // producer: one bulk copy per right-hand side and stage (16-byte multiple;
-    // the allocation of L carries a 64-byte tail for the last round-up)
-    int issued = 0;   // stages whose copies were issued (thread 0)
-    auto issue = [&](int ch) {
-        issued = ch + 1;
-        const int k = ch % kRing;
-        const int rows = min(kKS, a.nrow - ch * kKS);
-        const uint32_t bytes = ((uint32_t)(rows * a.ncol) * 8u + 15u) & ~15u;
-        const uint32_t fb = smem_u32(&cs.full[k]);
-        mbar_expect_tx(fb, bytes * (uint32_t)rgv);
-        for (int r = 0; r < rgv; ++r) {
-            const float2 *src = a.L + (int64_t)(rg0 + r) * a.vstride + (int64_t)leaf * a.mstride +
-                                (int64_t)ch * kKS * a.ncol;
-            bulk_g2s(smem_u32(ring + k * slot_c + r * kKS * a.ncol), src, bytes, fb);
-        }
-    };
-    if (tid == 0)
-        for (int ch = 0; ch < min(kRing, nch); ++ch) issue(ch);
-    // per-point phase tables e^{+i xi (x - c)} of the tile's points
-    for (int idx = tid; idx < kRows * a.rowlen; idx += kThreads) {
-        const int p = idx / a.rowlen, j = idx - p * a.rowlen;
-        E[p * a.rowpad + j] = p < cnt ? table_entry(a, a.xs + p0 + pt0 + p, a.N, j, c, 1.0f)
-                                      : make_float2(0.0f, 0.0f);
+    for (int idx = threadIdx.x; idx < np * rowpadE; idx += blockDim.x) {
+        const int p = idx / rowpadE, j = idx - p * rowpadE;
+        Eg[(p0 + p) * rowpadE + j] = j < a.rowlen ? table_entry(a, a.xs + p0 + p, a.N, j, c, -1.0f)
+                                                  : make_float2(0.0f, 0.0f);
     }
+    if (Lt)
+        for (int idx = threadIdx.x; idx < np * gpad; idx += blockDim.x) {
+            const int p = idx / gpad, r = idx - p * gpad;
+            Lt[(p0 + p) * gpad + r] = r < a.G ? a.lam[(int64_t)r * a.N + p0 + p] : 0.0f;
+        }
+}
+
+// ------------------------------------------------------------------ P2M ---
+// Persistent: CTA blockIdx.x takes the work items w = blockIdx.x + k gridDim.x,
+// w = (leaf * ntile1 + row tile) * ntile2 + column tile, with V_r[leaf][row *
+// ncol + col] as output.  NT = 16 NTH complex columns.  Epilogue warp w reads
+// TMEM lanes 32 (w & 3) .. and the complex columns [h NT/2, (h + 1) NT/2),
+// h = (w - kEpiWarp0) / 4.  The copy warp streams the stage's rows of the point
+// tables and coefficients into a ring of kRingE slots.  A mode row is (prefix,
+// k_{d-2}) with prefix = (k0, .., k_{d-3}); the prefix products of the tile's
+// prefixes are formed once per stage, so an A element costs one complex product.
+template <int NTH>
+__global__ void __launch_bounds__(kTcThreads, 1) k_p2m_tc(const TcArgs a, const float2 *Eg,
+                                                          const float *Lt, int rowpadE, int gpad,
+                                                          int ntile1, int ntile2, int nitems)
+{
+    constexpr int NT = 16 * NTH, NH = NT / 2, S = kP2MStages;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t wbytes = (uint32_t)(2 * NT) * kKStage * 4;
+    const uint32_t sbytes = kABytes + wbytes;
+    const int eslot = kKS * rowpadE, lslot = kKS * gpad;
+    float2 *Er = reinterpret_cast<float2 *>(smem + S * sbytes);       // [kRingE][kKS][rowpadE]
+    float *Lr = reinterpret_cast<float *>(Er + kRingE * eslot);        // [kRingE][kKS][gpad]
+    float2 *PF = reinterpret_cast<float2 *>(Lr + kRingE * lslot);      // [2][kKS][kPF]
+    const Sync y = sync_at(PF + 2 * kKS * kPF);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntot = a.ncol * a.G;
+    if (tid == 0) sync_init(y);
+    __syncwarp();
+    if (warp == 0) tmem_alloc(smem_u32(y.tslot), a.tcols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *cs.tslot;
+    const uint32_t tmem = *y.tslot;
 
-    // A side: this thread's point and mode-row quad; W side: (column, quad) pair
-    const int pa = tid & (kRows - 1), qa = tid >> 7;
-    const float2 *Ep = E + pa * a.rowpad;
-    const int jw = tid >> 1, qw = tid & 1;
-    const int rlw = jw / a.ncol, colw = jw - rlw * a.ncol;
-    const bool w_val = jw < ncolt && rlw < rgv;   // column present
-    // contraction with B'_i: lane quarter q (points), column half h
-    const int q = warp & 3, h = warp >> 2;
-    const int i = 32 * q + lane;
-    const uint32_t tlane = tmem + ((uint32_t)(32 * q) << 16);
-    const int ocol = a.d == 1 ? 0 : a.n0 + (a.d - 2) * a.n1;
-    const float2 *B = E + i * a.rowpad + ocol;
-    float acc[NH];
+    int gc = 0, gb = 0;          // stages and blocks of all items handled so far (per role)
+    int last = -1, issued = 0;   // last committed stage (MMA lane), stages copied (copy lane)
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const int ct = w % ntile2, rtile = (w / ntile2) % ntile1, leaf = w / (ntile2 * ntile1);
+        const int row0 = rtile * kRows, n0c = ct * NT;
+        const int64_t p0 = a.leaf_off[leaf];
+        const int np = a.leaf_off[leaf + 1] - (int)p0;
+        const int nch = (np + kKS - 1) / kKS;
+        if (warp < kProdWarps) {
+            // ---- producers
+            const int rt = tid & (kRows - 1), qa = tid >> 7;
+            const int row = row0 + rt;
+            const bool row_ok = row < a.nrow;
+            const int rlast = min(row0 + kRows, a.nrow) - 1;
+            const int qbase = a.d >= 3 ? row0 / a.n1 : 0;
+            const int npf = a.d >= 3 ? rlast / a.n1 - qbase + 1 : 0;
+            const int qloc = a.d >= 3 && row_ok ? row / a.n1 - qbase : 0;
+            const int oe = a.d >= 3 ? a.n0 + (a.d - 3) * a.n1 + (row_ok ? row % a.n1 : 0)
+                                    : (row_ok ? row : 0);
+            const int ocol = a.d == 1 ? 0 : a.n0 + (a.d - 2) * a.n1;
+            for (int lc = 0; lc < nch; ++lc, ++gc) {
+                const int s = gc % S, k = gc % kRingE;
+                if (gc >= S && !*y.abort) (void)wait_or_abort(&y.empty[s], ((gc - S) / S) & 1, y.abort);
+                if (!*y.abort) (void)wait_or_abort(&y.rfull[k], (uint32_t)(gc / kRingE) & 1u, y.abort);
+                const int cnt = min(kKS, np - lc * kKS);
+                const float2 *Ec = Er + k * eslot;
+                const float *Lc = Lr + k * lslot;
+                float2 *PFc = PF + (gc & 1) * kKS * kPF;
+                if (!*y.abort)
+                    for (int idx = tid; idx < kKS * npf; idx += kThreads) {
+                        const int p = idx / npf, q = idx - p * npf;
+                        PFc[p * kPF + q] = p < cnt ? prefix_phase(Ec + p * rowpadE, qbase + q, a.d,
+                                                                  a.n0, a.n1)
+                                                   : make_float2(0.0f, 0.0f);
+                    }
+                named_bar(kBarProd, kThreads);
+                if (!*y.abort) {
+                    unsigned char *tile = smem + s * sbytes;
+                    float re[4], im[4];
 #pragma unroll
-    for (int j = 0; j < NH; ++j) acc[j] = 0.0f;
-
-    auto gen = [&](int ch, unsigned char *tile) -> bool {
-        {
-            float re[4], im[4];
-            const int rw0 = ch * kKS + 4 * qa;
-            RowFac rf = row_factors(min(rw0, a.nrow - 1), a.d, a.n0, a.n1);
+                    for (int e = 0; e < 4; ++e) {
+                        const int p = 4 * qa + e;
+                        float2 v = make_float2(0.0f, 0.0f);
+                        if (row_ok && p < cnt) {
+                            if (a.d >= 3) v = cmul(PFc[p * kPF + qloc], Ec[p * rowpadE + oe]);
+                            else if (a.d == 2) v = Ec[p * rowpadE + oe];
+                            else v = make_float2(1.0f, 0.0f);
+                        }
+                        re[e] = v.x;
+                        im[e] = v.y;
+                    }
+                    put_a(tile, rt, qa, re, im);
+                    for (int idx = tid; idx < 2 * NT; idx += kThreads) {
+                        const int j = idx >> 1, qq = idx & 1;
+                        const int n = n0c + j;
+                        float wr[4] = {0, 0, 0, 0}, wi[4] = {0, 0, 0, 0};
+                        if (n < ntot) {
+                            const int r = n / a.ncol, col = n - r * a.ncol;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                float2 v = make_float2(0.0f, 0.0f);
-                if (rw0 + e < a.nrow) {
-                    v = row_phase(Ep, rf, a.d);
-                    row_next(rf, a.d, a.n0, a.n1);
+                            for (int e = 0; e < 4; ++e) {
+                                const int p = 4 * qq + e;
+                                if (p < cnt) {
+                                    const float2 ev = Ec[p * rowpadE + ocol + col];
+                                    const float l = Lc[p * gpad + r];
+                                    wr[e] = ev.x * l;
+                                    wi[e] = ev.y * l;
+                                }
+                            }
+                        }
+                        put_w(tile + kABytes, j, NT, qq, wr, wi);
+                    }
+                    fence_async_smem();
                 }
-                re[e] = v.x;
-                im[e] = v.y;
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(&y.full[s]));
+                    mbar_arrive(smem_u32(&y.rempty[k]));
+                }
             }
-            put_a(tile, pa, qa, re, im);
-        }
-        bool ok = true;
-        if (jw < NT) {
-            float wr[4] = {0, 0, 0, 0}, wi[4] = {0, 0, 0, 0};
-            if (w_val) {
-                const int k = ch % kRing;
-                ok = mbar_wait(smem_u32(&cs.full[k]), (uint32_t)(ch / kRing) & 1u);
-                const float2 *sl = ring + k * slot_c + rlw * kKS * a.ncol + colw;
+        } else if (warp == kMmaWarp) {
+            if (lane == 0) mma_item<S>(y, nch, gc, gb, last, smem, sbytes, tmem, a.idesc, NT);
+        } else if (warp == kCopyWarp) {
+            // ---- copies of the stage's table rows (cnt * rowpadE * 8 bytes) and
+            // coefficient rows (cnt * gpad * 4 bytes), multiples of 16
+            if (lane == 0) {
+                for (int lc = 0; lc < nch; ++lc, ++gc) {
+                    const int k = gc % kRingE;
+                    if (*y.abort) continue;
+                    if (gc >= kRingE &&
+                        !wait_or_abort(&y.rempty[k], (uint32_t)((gc - kRingE) / kRingE) & 1u, y.abort))
+                        continue;
+                    const int cnt = min(kKS, np - lc * kKS);
+                    const int64_t pt = p0 + (int64_t)lc * kKS;
+                    const uint32_t be = (uint32_t)(cnt * rowpadE) * 8u, bl = (uint32_t)(cnt * gpad) * 4u;
+                    const uint32_t fb = smem_u32(&y.rfull[k]);
+                    mbar_expect_tx(fb, be + bl);
+                    bulk_g2s(smem_u32(Er + k * eslot), Eg + pt * rowpadE, be, fb);
+                    bulk_g2s(smem_u32(Lr + k * lslot), Lt + pt * gpad, bl, fb);
+                    issued = gc + 1;
+                }
+            }
+        } else {
+            // ---- epilogue: blocks -> registers -> V
+            const int ew = warp - kEpiWarp0, q = warp & 3, h = ew >> 2;
+            const uint32_t tlane = tmem + ((uint32_t)(32 * q) << 16);
+            float acc_re[NH], acc_im[NH];
+            epi_item<NTH>(y, nch, gb, tlane, h, acc_re, acc_im);
+            const int row = row0 + 32 * q + lane;
+            if (!*y.abort && row < a.nrow) {
+                int n = n0c + h * NH;
+                int rhs = n / a.ncol, col = n - rhs * a.ncol;
+                float2 *out = a.V + (int64_t)leaf * a.mstride + (int64_t)row * a.ncol;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int rr = 4 * qw + e;
-                    if (ok && ch * kKS + rr < a.nrow) {
-                        const float2 v = sl[rr * a.ncol];
-                        wr[e] = v.x;
-                        wi[e] = v.y;
+                for (int j = 0; j < NH; ++j) {
+                    if (n + j < ntot)
+                        out[(int64_t)rhs * a.vstride + col] = make_float2(acc_re[j], acc_im[j]);
+                    if (++col == a.ncol) {
+                        col = 0;
+                        ++rhs;
                     }
                 }
             }
-            put_w(tile + kABytes, jw, NT, qw, wr, wi);
         }
-        return ok;
-    };
-    // every thread is done with slot ch % kRing: refill it for stage ch + kRing
-    auto post = [&](int ch) {
-        if (tid == 0 && ch + kRing < nch) issue(ch + kRing);
-    };
-    auto flush = [&](uint32_t col0) {
+    }
+    if (*y.abort) {   // bounded waits for the MMAs and copies still in flight
+        if (warp == kMmaWarp && lane == 0 && last >= 0)
+            wait_bounded(&y.empty[last % S], (uint32_t)(last / S) & 1u);
+        if (warp == kCopyWarp && lane == 0)
+            for (int c2 = max(0, issued - kRingE); c2 < issued; ++c2)
+                wait_bounded(&y.rfull[c2 % kRingE], (uint32_t)(c2 / kRingE) & 1u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, a.tcols);
+    }
+}
+
+// ------------------------------------------------------------------ L2P ---
+// Persistent: work item w = (leaf * nptile + point tile) * nrt + RHS tile; items
+// whose point tile is beyond the leaf are skipped by every role.  The tile's NT
+// = 16 NTH complex columns hold Rg whole right-hand sides (Rg * ncol <= NT), so
+// every u_{i,r} is finished in the CTA.  The kKS-row slices of L_r
+// (contiguous: rows are row-major) arrive through a ring of kRingL slots filled
+// by the copy warp.  At the end of an item the epilogue contracts T with
+// B'_i = conj(E_{d-1}[i]) (from the point tables) and sums the columns of each
+// right-hand side in column order.
+template <int NTH>
+__global__ void __launch_bounds__(kTcThreads, 1) k_l2p_tc(const TcArgs a, const float2 *Eg,
+                                                          int rowpadE, int Rg, int nptile, int nrt,
+                                                          int nitems)
+{
+    constexpr int NT = 16 * NTH, NH = NT / 2, S = kL2PStages;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t wbytes = (uint32_t)(2 * NT) * kKStage * 4;
+    const uint32_t sbytes = kABytes + wbytes;
+    const int slot_c = Rg * kKS * a.ncol;                              // complex per ring slot
+    float2 *ring = reinterpret_cast<float2 *>(smem + S * sbytes);      // [kRingL][Rg][kKS][ncol]
+    float2 *E = ring + kRingL * slot_c;                                // [kRows][rowpad]
+    float *Sg = reinterpret_cast<float *>(E + kRows * a.rowpad);       // [kRows][2][Rg]
+    const Sync y = sync_at(Sg + kRows * 2 * Rg);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ncolt = Rg * a.ncol;        // columns of the tile
+    const int nch = (a.nrow + kKS - 1) / kKS;
+    if (tid == 0) sync_init(y);
+    __syncwarp();
+    if (warp == 0) tmem_alloc(smem_u32(y.tslot), a.tcols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *y.tslot;
+
+    int gc = 0, gb = 0;          // stages and blocks of all items handled so far (per role)
+    int last = -1, issued = 0;   // last committed stage (MMA lane), stages copied (copy lane)
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        const int rt_ = w % nrt, ptile = (w / nrt) % nptile, leaf = w / (nrt * nptile);
+        const int64_t p0 = a.leaf_off[leaf];
+        const int np = a.leaf_off[leaf + 1] - (int)p0;
+        const int pt0 = ptile * kRows;
+        if (pt0 >= np) continue;   // same decision in every role
+        const int cnt = min(kRows, np - pt0);
+        const int rg0 = rt_ * Rg;
+        const int rgv = min(Rg, a.G - rg0);
+        if (warp < kProdWarps) {
+            // ---- producers: per-point phases e^{+i xi (x - c)} of the item, then stages
+            double c[RBF_MAX_DIM];
+            leaf_centre(a, leaf, c);
+            named_bar(kBarProd, kThreads);   // every producer is done with the previous item
+            for (int idx = tid; idx < kRows * a.rowlen; idx += kThreads) {
+                const int p = idx / a.rowlen, j = idx - p * a.rowlen;
+                E[p * a.rowpad + j] = p < cnt ? table_entry(a, a.xs + p0 + pt0 + p, a.N, j, c, 1.0f)
+                                              : make_float2(0.0f, 0.0f);
+            }
+            named_bar(kBarProd, kThreads);
+            const int pa = tid & (kRows - 1), qa = tid >> 7;
+            const float2 *Ep = E + pa * a.rowpad;
+            const int jw = tid >> 1, qw = tid & 1;
+            const int rlw = jw / a.ncol, colw = jw - rlw * a.ncol;
+            const bool w_on = jw < NT;
+            const bool w_val = jw < ncolt && rlw < rgv;
+            const float2 *Elast = Ep + (a.d >= 3 ? a.n0 + (a.d - 3) * a.n1 : 0);
+            for (int lc = 0; lc < nch; ++lc, ++gc) {
+                const int s = gc % S, k = gc % kRingL;
+                if (gc >= S && !*y.abort) (void)wait_or_abort(&y.empty[s], ((gc - S) / S) & 1, y.abort);
+                unsigned char *tile = smem + s * sbytes;
+                if (!*y.abort && w_on) {
+                    float wr[4] = {0, 0, 0, 0}, wi[4] = {0, 0, 0, 0};
+                    if (w_val && wait_or_abort(&y.rfull[k], (uint32_t)(gc / kRingL) & 1u, y.abort)) {
+                        const float2 *sl = ring + k * slot_c + rlw * kKS * a.ncol + colw;
 #pragma unroll
-        for (int g = 0; g < NTH; ++g) {
-            float re[8], im[8];
-            tmem_ld8(tlane + col0 + h * NH + 8 * g, re);
-            tmem_ld8(tlane + col0 + NT + h * NH + 8 * g, im);
-            tmem_wait_ld();
+                        for (int e = 0; e < 4; ++e) {
+                            const int rr = 4 * qw + e;
+                            if (lc * kKS + rr < a.nrow) {
+                                const float2 v = sl[rr * a.ncol];
+                                wr[e] = v.x;
+                                wi[e] = v.y;
+                            }
+                        }
+                    }
+                    put_w(tile + kABytes, jw, NT, qw, wr, wi);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&y.rempty[k]));
+                if (!*y.abort) {
+                    // row = (prefix Q, k_{d-2}): A'_i[row] = PF_i(Q) E_{d-2}[i][k_{d-2}],
+                    // the prefix product formed again only when Q changes
+                    float re[4], im[4];
+                    const int rw0 = lc * kKS + 4 * qa;
+                    int Q = a.d >= 3 ? rw0 / a.n1 : 0, kl = a.d >= 3 ? rw0 - Q * a.n1 : 0;
+                    float2 pf = a.d >= 3 && rw0 < a.nrow ? prefix_phase(Ep, Q, a.d, a.n0, a.n1)
+                                                          : make_float2(1.0f, 0.0f);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int j = h * NH + 8 * g + e;
-                if (j < ncolt) {
-                    const float2 b = B[j % a.ncol];
-                    acc[8 * g + e] = fmaf(b.x, re[e], acc[8 * g + e]);
-                    acc[8 * g + e] = fmaf(-b.y, im[e], acc[8 * g + e]);
+                    for (int e = 0; e < 4; ++e) {
+                        const int rw = rw0 + e;
+                        float2 v = make_float2(0.0f, 0.0f);
+                        if (rw < a.nrow) {
+                            if (a.d >= 3) {
+                                v = cmul(pf, Elast[kl]);
+                                if (++kl == a.n1 && rw + 1 < a.nrow) {
+                                    kl = 0;
+                                    pf = prefix_phase(Ep, ++Q, a.d, a.n0, a.n1);
+                                }
+                            } else if (a.d == 2) {
+                                v = Ep[rw];
+                            } else {
+                                v = make_float2(1.0f, 0.0f);
+                            }
+                        }
+                        re[e] = v.x;
+                        im[e] = v.y;
+                    }
+                    put_a(tile, pa, qa, re, im);
+                    fence_async_smem();
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&y.full[s]));
+            }
+        } else if (warp == kMmaWarp) {
+            if (lane == 0) mma_item<S>(y, nch, gc, gb, last, smem, sbytes, tmem, a.idesc, NT);
+        } else if (warp == kCopyWarp) {
+            // ---- copies: one bulk copy per right-hand side and stage (16-byte
+            // multiple; the allocation of L carries a 64-byte tail for the round-up)
+            if (lane == 0) {
+                for (int lc = 0; lc < nch; ++lc, ++gc) {
+                    const int k = gc % kRingL;
+                    if (*y.abort) continue;
+                    if (gc >= kRingL &&
+                        !wait_or_abort(&y.rempty[k], (uint32_t)((gc - kRingL) / kRingL) & 1u, y.abort))
+                        continue;
+                    const int rows = min(kKS, a.nrow - lc * kKS);
+                    const uint32_t bytes = ((uint32_t)(rows * a.ncol) * 8u + 15u) & ~15u;
+                    const uint32_t fb = smem_u32(&y.rfull[k]);
+                    mbar_expect_tx(fb, bytes * (uint32_t)rgv);
+                    for (int r = 0; r < rgv; ++r) {
+                        const float2 *src = a.L + (int64_t)(rg0 + r) * a.vstride +
+                                            (int64_t)leaf * a.mstride + (int64_t)lc * kKS * a.ncol;
+                        bulk_g2s(smem_u32(ring + k * slot_c + r * kKS * a.ncol), src, bytes, fb);
+                    }
+                    issued = gc + 1;
                 }
             }
-        }
-    };
-    const bool ok = tc_pipeline(nch, SL, tmem, a.idesc, NT, cs.bar, gen, post, flush);
-    if (ok) {
-        // per-column sums -> shared [kRows][NT + 1] -> per-RHS sums in column order
-        __syncthreads();
-        float *S = reinterpret_cast<float *>(smem);
-        const int sst = NT + 1;
+        } else {
+            // ---- epilogue
+            const int ew = warp - kEpiWarp0, q = warp & 3, h = ew >> 2;
+            const int i = 32 * q + lane;
+            const uint32_t tlane = tmem + ((uint32_t)(32 * q) << 16);
+            float acc_re[NH], acc_im[NH];
+            epi_item<NTH>(y, nch, gb, tlane, h, acc_re, acc_im);
+            // S_i[h][r] = sum over this half's columns of r of Re(B'_i[col] T_i[col, r])
+            const int ocol = a.d == 1 ? 0 : a.n0 + (a.d - 2) * a.n1;
+            float *Si = Sg + (i * 2 + h) * Rg;
+            for (int r = 0; r < Rg; ++r) Si[r] = 0.0f;
+            if (!*y.abort && i < cnt) {
+                const float2 *B = Eg + (p0 + pt0 + i) * rowpadE + ocol;   // conj gives B'
+                int j = h * NH, rl = j / a.ncol, col = j - rl * a.ncol;
 #pragma unroll
-        for (int j = 0; j < NH; ++j) S[i * sst + h * NH + j] = acc[j];
-        __syncthreads();
-        for (int idx = tid; idx < kRows * rgv; idx += kThreads) {
-            const int pi = idx % kRows, rl = idx / kRows;
-            if (pi >= cnt) continue;
-            float u = 0.0f;
-            for (int col = 0; col < a.ncol; ++col) u += S[pi * sst + rl * a.ncol + col];
-            a.u[(int64_t)(rg0 + rl) * a.N + p0 + pt0 + pi] = u;
+                for (int jj = 0; jj < NH; ++jj, ++j) {
+                    if (j < ncolt) {
+                        const float2 bb = B[col];   // B' = (bb.x, -bb.y)
+                        Si[rl] += fmaf(bb.x, acc_re[jj], bb.y * acc_im[jj]);
+                    }
+                    if (++col == a.ncol) {
+                        col = 0;
+                        ++rl;
+                    }
+                }
+            }
+            named_bar(kBarEpi, 32 * kEpiWarps);
+            if (!*y.abort) {
+                const int et = tid - 32 * kEpiWarp0;
+                for (int idx = et; idx < kRows * rgv; idx += 32 * kEpiWarps) {
+                    const int pi = idx % kRows, rl = idx / kRows;
+                    if (pi < cnt)
+                        a.u[(int64_t)(rg0 + rl) * a.N + p0 + pt0 + pi] =
+                            Sg[(pi * 2) * Rg + rl] + Sg[(pi * 2 + 1) * Rg + rl];
+                }
+            }
+            named_bar(kBarEpi, 32 * kEpiWarps);
         }
-    } else {
-        drain(cs, nch);
-        // bounded wait for the copies in flight: the latest issued phase of each slot
-        if (tid == 0)
-            for (int ch = std::max(0, issued - kRing); ch < issued; ++ch)
-                (void)mbar_wait(smem_u32(&cs.full[ch % kRing]), (uint32_t)(ch / kRing) & 1u);
     }
-    cta_teardown(tmem, a.tcols);
+    if (*y.abort) {   // bounded waits for the MMAs and copies still in flight
+        if (warp == kMmaWarp && lane == 0 && last >= 0)
+            wait_bounded(&y.empty[last % S], (uint32_t)(last / S) & 1u);
+        if (warp == kCopyWarp && lane == 0)
+            for (int c2 = max(0, issued - kRingL); c2 < issued; ++c2)
+                wait_bounded(&y.rfull[c2 % kRingL], (uint32_t)(c2 / kRingL) & 1u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, a.tcols);
+    }
 }
 
 inline uint32_t tmem_cols(int n)
@@ -800,7 +897,6 @@ TcArgs base_args(const rbf_tree *t, const rbf_plan *p, int G)
     a.G = G;
     a.rowlen = t->d == 1 ? p->n0 : p->n0 + (t->d - 1) * p->n1;
     a.rowpad = a.rowlen | 1;
-    a.lcap = std::max(1, (int)t->max_leaf);
     a.mstride = p->mstride;
     a.N = t->N;
     a.vstride = (int64_t)t->nleaf() * p->mstride;
@@ -814,7 +910,12 @@ TcArgs base_args(const rbf_tree *t, const rbf_plan *p, int G)
 }
 
 constexpr size_t kSmemMax = 227 * 1024;
-size_t stage_bytes(int NT) { return 2 * ((size_t)kABytes + (size_t)2 * NT * kKStage * 4); }
+size_t stage_bytes(int NT, int S) { return (size_t)S * ((size_t)kABytes + (size_t)2 * NT * kKStage * 4); }
+inline int rowpad_even(const rbf_tree *t, const rbf_plan *p)
+{
+    const int rowlen = t->d == 1 ? p->n0 : p->n0 + (t->d - 1) * p->n1;
+    return (rowlen + 1) & ~1;
+}
 
 // P2M tile: complex columns per tile (16 NTH) and shared memory
 void p2m_shape(const rbf_tree *t, const rbf_plan *p, int G, int *nth, size_t *smem)
@@ -831,9 +932,10 @@ void p2m_shape(const rbf_tree *t, const rbf_plan *p, int G, int *nth, size_t *sm
         }
     }
     *nth = best_c;
-    const int rowlen = t->d == 1 ? p->n0 : p->n0 + (t->d - 1) * p->n1;
-    *smem = stage_bytes(16 * best_c) + (size_t)kKS * rowlen * sizeof(float2) +
-            (size_t)(t->d + G) * std::max(1, (int)t->max_leaf) * sizeof(float) + kSyncBytes;
+    const int gpad = 16;   // coefficient columns of the point-major copy
+    *smem = stage_bytes(16 * best_c, kP2MStages) +
+            (size_t)kRingE * kKS * (rowpad_even(t, p) * sizeof(float2) + gpad * sizeof(float)) +
+            (size_t)2 * kKS * kPF * sizeof(float2) + kSyncBytes;
 }
 
 // L2P tile: right-hand sides per tile, complex columns (16 NTH) and shared memory
@@ -845,26 +947,43 @@ void l2p_shape(const rbf_tree *t, const rbf_plan *p, int G, int *rg, int *nth, s
     *rg = Rg;
     *nth = (Rg * p->ncol + 15) / 16;
     const int rowlen = t->d == 1 ? p->n0 : p->n0 + (t->d - 1) * p->n1;
-    *smem = stage_bytes(16 * *nth) + (size_t)kRing * Rg * kKS * p->ncol * sizeof(float2) +
-            (size_t)kRows * (rowlen | 1) * sizeof(float2) + kSyncBytes;
+    *smem = stage_bytes(16 * *nth, kL2PStages) + (size_t)kRingL * Rg * kKS * p->ncol * sizeof(float2) +
+            (size_t)kRows * (rowlen | 1) * sizeof(float2) + (size_t)kRows * 2 * Rg * sizeof(float) +
+            kSyncBytes;
+}
+
+int num_sms()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 152;
+    }
+    return n;
 }
 
 template <int NTH>
-int launch_p2m(const TcArgs &a, dim3 grid, size_t smem, cudaStream_t s)
+int launch_p2m(const TcArgs &a, const float2 *Eg, const float *Lt, int rowpadE, int gpad,
+               int ntile1, int ntile2, int nitems, size_t smem, cudaStream_t s)
 {
     RBF_CUDA_TRY(cudaFuncSetAttribute(k_p2m_tc<NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-    k_p2m_tc<NTH><<<grid, kThreads, smem, s>>>(a);
+    const int grid = std::min(nitems, num_sms());
+    k_p2m_tc<NTH><<<grid, kTcThreads, smem, s>>>(a, Eg, Lt, rowpadE, gpad, ntile1, ntile2, nitems);
     RBF_LAUNCH_CHECK();
     return RBF_OK;
 }
 
 template <int NTH>
-int launch_l2p(const TcArgs &a, int Rg, dim3 grid, size_t smem, cudaStream_t s)
+int launch_l2p(const TcArgs &a, const float2 *Eg, int rowpadE, int Rg, int nptile, int nrt,
+               int nitems, size_t smem, cudaStream_t s)
 {
     RBF_CUDA_TRY(cudaFuncSetAttribute(k_l2p_tc<NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-    k_l2p_tc<NTH><<<grid, kThreads, smem, s>>>(a, Rg);
+    const int grid = std::min(nitems, num_sms());
+    k_l2p_tc<NTH><<<grid, kTcThreads, smem, s>>>(a, Eg, rowpadE, Rg, nptile, nrt, nitems);
     RBF_LAUNCH_CHECK();
     return RBF_OK;
 }
@@ -873,35 +992,48 @@ int launch_l2p(const TcArgs &a, int Rg, dim3 grid, size_t smem, cudaStream_t s)
 
 int rbf_far_multi_supported(const rbf_plan *p) { return p->ncol <= kMaxNT; }
 
-int rbf_run_far_multi(rbf_tree *t, const rbf_plan *p, const float *lam_s, int G, float2 *V,
-                      float2 *L, float *u_far, cudaStream_t s)
+int rbf_run_far_multi(rbf_tree *t, rbf_plan *p, const float *lam_s, int G, float2 *V, float2 *L,
+                      float *u_far, cudaStream_t s)
 {
-    RBF_REQUIRE(G >= 1 && p->ncol <= kMaxNT, "rbf_run_far_multi: G=%d, %d columns", G, p->ncol);
+    RBF_REQUIRE(G >= 1 && G <= 16 && p->ncol <= kMaxNT, "rbf_run_far_multi: G=%d, %d columns", G,
+                p->ncol);
     const int nleaf = t->nleaf();
     const int64_t vstride = (int64_t)nleaf * p->mstride;
     // The tensor-core contractions pay off when a leaf fills the K dimension
     // (P2M: points) or the M dimension (L2P: points per 128-row tile); with
     // fewer points per leaf the CUDA-core kernels run column by column.
     const double per_leaf = (double)t->N / std::max(1, nleaf);
-    int nth = 0;
-    size_t smem = 0;
-    p2m_shape(t, p, G, &nth, &smem);
-    if (per_leaf >= 64.0 && smem <= kSmemMax) {
+    int nth_p = 0, nth_l = 0, Rg = 0;
+    size_t smem_p = 0, smem_l = 0;
+    p2m_shape(t, p, G, &nth_p, &smem_p);
+    l2p_shape(t, p, G, &Rg, &nth_l, &smem_l);
+    const bool tc_p2m = per_leaf >= 64.0 && smem_p <= kSmemMax;
+    const bool tc_l2p = per_leaf >= 96.0 && smem_l <= kSmemMax;
+    const int rowpadE = rowpad_even(t, p);
+    const int gpad = 16;   // coefficient rows of the point-major copy (G <= 16)
+    if (tc_p2m || tc_l2p) {
+        if (!p->mr_E) RBF_TRY(rbf_alloc(&p->mr_E, (size_t)t->N * rowpadE));
+        if (tc_p2m && !p->mr_Lt) RBF_TRY(rbf_alloc(&p->mr_Lt, (size_t)t->N * gpad));
         TcArgs a = base_args(t, p, G);
         a.lam = lam_s;
+        k_point_tables<<<nleaf, 256, 0, s>>>(a, rowpadE, p->mr_E, gpad, tc_p2m ? p->mr_Lt : nullptr);
+        RBF_LAUNCH_CHECK();
+    }
+    if (tc_p2m) {
+        TcArgs a = base_args(t, p, G);
         a.V = V;
-        a.NT = 16 * nth;
+        a.NT = 16 * nth_p;
         a.idesc = instr_desc_tf32(kRows, 2 * a.NT);
         a.tcols = tmem_cols(4 * a.NT);
-        const int ntiles = (p->ncol * G + a.NT - 1) / a.NT;
-        dim3 grid(nleaf, ceil_div(p->nrow, kRows), ntiles);
-        RBF_REQUIRE(grid.y < 65536 && grid.z < 65536, "rbf_run_far_multi: expansion too large");
+        const int ntile1 = ceil_div(p->nrow, kRows), ntile2 = ceil_div((int64_t)p->ncol * G, a.NT);
+        const int64_t nitems = (int64_t)nleaf * ntile1 * ntile2;
+        RBF_REQUIRE(nitems < INT32_MAX, "rbf_run_far_multi: too many tiles");
         rbf_pass_timer tm(t, RBF_PASS_P2M, s);
-        switch (nth) {
-        case 1: RBF_TRY(launch_p2m<1>(a, grid, smem, s)); break;
-        case 2: RBF_TRY(launch_p2m<2>(a, grid, smem, s)); break;
-        case 3: RBF_TRY(launch_p2m<3>(a, grid, smem, s)); break;
-        default: RBF_TRY(launch_p2m<4>(a, grid, smem, s)); break;
+        switch (nth_p) {
+        case 1: RBF_TRY(launch_p2m<1>(a, p->mr_E, p->mr_Lt, rowpadE, gpad, ntile1, ntile2, (int)nitems, smem_p, s)); break;
+        case 2: RBF_TRY(launch_p2m<2>(a, p->mr_E, p->mr_Lt, rowpadE, gpad, ntile1, ntile2, (int)nitems, smem_p, s)); break;
+        case 3: RBF_TRY(launch_p2m<3>(a, p->mr_E, p->mr_Lt, rowpadE, gpad, ntile1, ntile2, (int)nitems, smem_p, s)); break;
+        default: RBF_TRY(launch_p2m<4>(a, p->mr_E, p->mr_Lt, rowpadE, gpad, ntile1, ntile2, (int)nitems, smem_p, s)); break;
         }
     } else {
         for (int g = 0; g < G; ++g)
@@ -911,24 +1043,23 @@ int rbf_run_far_multi(rbf_tree *t, const rbf_plan *p, const float *lam_s, int G,
         RBF_TRY(rbf_run_m2m<float>(t, p, V + g * vstride, s));
         RBF_TRY(rbf_run_m2l<float>(t, p, V + g * vstride, L + g * vstride, s));
     }
-    int Rg = 0;
-    l2p_shape(t, p, G, &Rg, &nth, &smem);
-    if (per_leaf >= 96.0 && smem <= kSmemMax) {
+    if (tc_l2p) {
         TcArgs a = base_args(t, p, G);
         a.L = L;
         a.u = u_far;
-        a.NT = 16 * nth;
+        a.NT = 16 * nth_l;
         a.idesc = instr_desc_tf32(kRows, 2 * a.NT);
         a.tcols = tmem_cols(4 * a.NT);
-        const int rtiles = (G + Rg - 1) / Rg;
-        dim3 grid(nleaf, ceil_div(std::max<int>(t->max_leaf, 1), kRows), rtiles);
-        RBF_REQUIRE(grid.y < 65536, "rbf_run_far_multi: leaf too large");
+        const int nrt = (G + Rg - 1) / Rg;
+        const int nptile = ceil_div(std::max<int>(t->max_leaf, 1), kRows);
+        const int64_t nitems = (int64_t)nleaf * nptile * nrt;
+        RBF_REQUIRE(nitems < INT32_MAX, "rbf_run_far_multi: too many tiles");
         rbf_pass_timer tm(t, RBF_PASS_L2P, s);
-        switch (nth) {
-        case 1: RBF_TRY(launch_l2p<1>(a, Rg, grid, smem, s)); break;
-        case 2: RBF_TRY(launch_l2p<2>(a, Rg, grid, smem, s)); break;
-        case 3: RBF_TRY(launch_l2p<3>(a, Rg, grid, smem, s)); break;
-        default: RBF_TRY(launch_l2p<4>(a, Rg, grid, smem, s)); break;
+        switch (nth_l) {
+        case 1: RBF_TRY(launch_l2p<1>(a, p->mr_E, rowpadE, Rg, nptile, nrt, (int)nitems, smem_l, s)); break;
+        case 2: RBF_TRY(launch_l2p<2>(a, p->mr_E, rowpadE, Rg, nptile, nrt, (int)nitems, smem_l, s)); break;
+        case 3: RBF_TRY(launch_l2p<3>(a, p->mr_E, rowpadE, Rg, nptile, nrt, (int)nitems, smem_l, s)); break;
+        default: RBF_TRY(launch_l2p<4>(a, p->mr_E, rowpadE, Rg, nptile, nrt, (int)nitems, smem_l, s)); break;
         }
     } else {
         for (int g = 0; g < G; ++g)

@@ -189,6 +189,8 @@ void rbf_plan_free(rbf_plan *p)
     rbf_free(p->mr_lam);
     rbf_free(p->mr_un);
     rbf_free(p->mr_uf);
+    rbf_free(p->mr_E);
+    rbf_free(p->mr_Lt);
     delete p;
 }
 

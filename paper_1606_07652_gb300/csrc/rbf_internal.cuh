@@ -205,6 +205,8 @@ struct rbf_plan {
     float *mr_lam = nullptr;   // [mr_G][N]
     float *mr_un = nullptr;    // [mr_G][N]
     float *mr_uf = nullptr;    // [mr_G][N]
+    float2 *mr_E = nullptr;    // [N][even_up(n0 + (d-1) n1)] point phase tables of P2M
+    float *mr_Lt = nullptr;    // [N][16] coefficients of a group, point-major
 };
 
 int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_params *p, int prec,
@@ -231,8 +233,8 @@ template <typename R>
 int rbf_run_m2l(rbf_tree *t, const rbf_plan *p, const cplx<R> *VD, cplx<R> *L, cudaStream_t s);
 // FP32 far field of G right-hand sides at once: P2M and L2P on the tensor cores
 // (far_mrhs.cu); lam_s and u_far are [G][N], V and L are [G][nleaf][mstride]
-int rbf_run_far_multi(rbf_tree *t, const rbf_plan *p, const float *lam_s, int G, float2 *V,
-                      float2 *L, float *u_far, cudaStream_t s);
+int rbf_run_far_multi(rbf_tree *t, rbf_plan *p, const float *lam_s, int G, float2 *V, float2 *L,
+                      float *u_far, cudaStream_t s);
 // nonzero when the plan's columns per mode row fit a tensor-core tile
 int rbf_far_multi_supported(const rbf_plan *p);
 // nonzero when a bounded device-side wait of a tensor-core kernel gave up
