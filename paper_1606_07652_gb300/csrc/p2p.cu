@@ -14,9 +14,16 @@ namespace {
 
 constexpr int P2P_THREADS = 128;
 constexpr int P2P_WARPS = P2P_THREADS / 32;
-constexpr int P2P_TGROUPS = 8;                 // target groups of 32 per pass
-constexpr int P2P_TBLOCK = 32 * P2P_TGROUPS;   // targets per pass
 constexpr int P2P_STAGE_BYTES = 16384;         // shared memory for staged sources
+#ifndef RBF_P2P_SU
+#define RBF_P2P_SU 4                           // sources per step (independent partial sums)
+#endif
+#ifndef RBF_P2P_TGMAX
+#define RBF_P2P_TGMAX 4                        // target groups of 32 per pass, at most
+#endif
+#ifndef RBF_P2P_SMALL
+#define RBF_P2P_SMALL 64                       // leaves up to this size: one group per pass
+#endif
 
 template <typename R>
 struct Src4;
@@ -40,7 +47,7 @@ __device__ __forceinline__ double phi_r2(int kernel, double e2, double r2)
     return kernel == RBF_GAUSSIAN ? exp(-e2 * r2) : rsqrt(fma(e2, r2, 1.0));
 }
 
-template <typename R, int DIM>
+template <typename R, int DIM, int TG>
 __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int kernel, R e2, int64_t N, const R *xs,
                                                      const R *lam, const int32_t *leaf_off,
                                                      const int32_t *near_off,
@@ -50,9 +57,11 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int kernel, R e2, int64_t N
     // per source: (x0, x1, x2, lambda) for DIM <= 3; DIM > 3 uses two records
     constexpr int REC = DIM <= 3 ? 1 : 2;
     constexpr int P2P_SCHUNK = P2P_STAGE_BYTES / (int)(sizeof(S4) * REC);
+    constexpr int TB = 32 * TG;   // targets per pass
+    constexpr int SU = RBF_P2P_SU;   // sources per iteration, one partial sum each
     __shared__ S4 src[P2P_SCHUNK * REC];
     __shared__ int32_t rstart[729], rlen[729], rpre[730];
-    __shared__ R red[P2P_WARPS][P2P_TBLOCK];
+    __shared__ R red[P2P_WARPS][TB];
     const int a = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int e0 = near_off[a], ne = near_off[a + 1] - e0;
@@ -70,13 +79,14 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int kernel, R e2, int64_t N
     __syncthreads();
     const int nsrc = rpre[ne];
     const int t0 = leaf_off[a], nt = leaf_off[a + 1] - t0;
-    for (int tb = 0; tb < nt; tb += P2P_TBLOCK) {
-        R xt[P2P_TGROUPS][DIM];
-        R acc[P2P_TGROUPS];
+    for (int tb = 0; tb < nt; tb += TB) {
+        R xt[TG][DIM];
+        R acc[TG][SU];
 #pragma unroll
-        for (int g = 0; g < P2P_TGROUPS; ++g) {
+        for (int g = 0; g < TG; ++g) {
             int i = tb + g * 32 + lane;
-            acc[g] = (R)0;
+#pragma unroll
+            for (int k = 0; k < SU; ++k) acc[g][k] = (R)0;
 #pragma unroll
             for (int t = 0; t < DIM; ++t) xt[g][t] = i < nt ? xs[(int64_t)t * N + t0 + i] : (R)0;
         }
@@ -117,15 +127,27 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int kernel, R e2, int64_t N
                     src[2 * v + 1] = r1;
                 }
             }
+            // pad the chunk to a multiple of SU sources per warp stride with zero weights
+            for (int v = cnt + threadIdx.x; v < cnt + P2P_WARPS * SU; v += P2P_THREADS) {
+                if (v < P2P_SCHUNK) {
+                    S4 z;
+                    z.x = z.y = z.z = z.w = (R)0;
+                    src[REC * v] = z;
+                    if (REC == 2) src[REC * v + 1] = z;
+                }
+            }
             __syncthreads();
-            const int ngrp = min(P2P_TGROUPS, (nt - tb + 31) / 32);
-            for (int j = warp; j < cnt; j += P2P_WARPS) {
-                S4 r0 = src[REC * j];
-                S4 r1;
-                if (REC == 2) r1 = src[2 * j + 1];
+            // warp w takes sources w*SU + k + j*(WARPS*SU), k < SU: SU independent pairs per step
+            for (int j0 = warp * SU; j0 < cnt; j0 += P2P_WARPS * SU) {
 #pragma unroll
-                for (int g = 0; g < P2P_TGROUPS; ++g) {
-                    if (g < ngrp) {
+                for (int k = 0; k < SU; ++k) {
+                    const int j = min(j0 + k, P2P_SCHUNK - 1);
+                    const S4 r0 = src[REC * j];
+                    S4 r1;
+                    if (REC == 2) r1 = src[REC * j + 1];
+                    const R wgt = j0 + k < cnt ? r0.w : (R)0;
+#pragma unroll
+                    for (int g = 0; g < TG; ++g) {
                         R d0 = xt[g][0] - r0.x;
                         R r2 = d0 * d0;
                         if (DIM > 1) {
@@ -148,16 +170,22 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int kernel, R e2, int64_t N
                             R d5 = xt[g][DIM > 5 ? 5 : 0] - r1.z;
                             r2 = fma(d5, d5, r2);
                         }
-                        acc[g] = fma(r0.w, phi_r2(kernel, e2, r2), acc[g]);
+                        acc[g][k] = fma(wgt, phi_r2(kernel, e2, r2), acc[g][k]);
                     }
                 }
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int g = 0; g < P2P_TGROUPS; ++g) red[warp][g * 32 + lane] = acc[g];
+        for (int g = 0; g < TG; ++g)
+        {
+            R t = acc[g][0];
+#pragma unroll
+            for (int k = 1; k < SU; ++k) t += acc[g][k];
+            red[warp][g * 32 + lane] = t;
+        }
         __syncthreads();
-        for (int i = threadIdx.x; i < min(P2P_TBLOCK, nt - tb); i += P2P_THREADS) {
+        for (int i = threadIdx.x; i < min(TB, nt - tb); i += P2P_THREADS) {
             R s = red[0][i];
 #pragma unroll
             for (int w = 1; w < P2P_WARPS; ++w) s += red[w][i];
@@ -166,16 +194,16 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int kernel, R e2, int64_t N
     }
 }
 
-template <typename R>
-int launch_p2p(int d, int kernel, R e2, const rbf_tree *t, const R *xs, const R *lam, R *u,
-               cudaStream_t s)
+template <typename R, int TG>
+int launch_p2p_tg(int d, int kernel, R e2, const rbf_tree *t, const R *xs, const R *lam, R *u,
+                  cudaStream_t s)
 {
     const int nleaf = t->nleaf();
     switch (d) {
 #define RBF_P2P_CASE(DD)                                                                          \
     case DD:                                                                                      \
-        k_p2p<R, DD><<<nleaf, P2P_THREADS, 0, s>>>(kernel, e2, t->N, xs, lam, t->leaf_off,         \
-                                                   t->near_off, t->near_idx, u);                   \
+        k_p2p<R, DD, TG><<<nleaf, P2P_THREADS, 0, s>>>(kernel, e2, t->N, xs, lam, t->leaf_off,     \
+                                                       t->near_off, t->near_idx, u);               \
         break;
         RBF_P2P_CASE(1)
         RBF_P2P_CASE(2)
@@ -190,6 +218,18 @@ int launch_p2p(int d, int kernel, R e2, const rbf_tree *t, const R *xs, const R 
     }
     RBF_LAUNCH_CHECK();
     return RBF_OK;
+}
+
+// target groups of 32 per pass: one for small leaves (a leaf of up to 64 points takes
+// two passes rather than a half-empty second group), four for large leaves
+template <typename R>
+int launch_p2p(int d, int kernel, R e2, const rbf_tree *t, const R *xs, const R *lam, R *u,
+               cudaStream_t s)
+{
+    const int ml = std::max<int>(1, t->max_leaf);
+    if (ml <= RBF_P2P_SMALL || RBF_P2P_TGMAX == 1)
+        return launch_p2p_tg<R, 1>(d, kernel, e2, t, xs, lam, u, s);
+    return launch_p2p_tg<R, 4>(d, kernel, e2, t, xs, lam, u, s);
 }
 
 // ---------------------------------------------- several right-hand sides --
