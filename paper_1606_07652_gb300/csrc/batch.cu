@@ -207,36 +207,35 @@ extern "C" int rbf_autotune(rbf_kernel kernel, double eps, int d, int64_t N, dou
         p.period_L = 4.0 * side;
     }
     // expansion order: the smallest even M in [8, 64] whose measured far-kernel error
-    // meets tol (bisection; the error falls with M), else 64
+    // meets tol (the error falls with M), else 64.  The search starts from the M at
+    // which the kernel's Fourier transform has decayed to tol at the band edge
+    // pi M / L (Gaussian: exp(-xi^2 / (4 eps^2)); inverse multiquadric: ~exp(-xi / eps))
+    // and steps by 2.
     auto error_at = [&](int M, double *e) -> int {
         p.M = M;
         return rbf_kernel_error(kernel, eps, d, &p, side, D, e);
     };
+    const double lt = std::log(1.0 / tol);
+    const double pred = kernel == RBF_GAUSSIAN ? 2.0 * eps * p.period_L * std::sqrt(lt) / M_PI
+                                               : eps * p.period_L * lt / M_PI;
+    int M0 = 2 * (int)std::lround(pred / 2.0);
+    M0 = std::max(8, std::min(64, M0));
     double err = INFINITY;
-    RBF_TRY(error_at(64, &err));
-    int Mbest = 64;
+    RBF_TRY(error_at(M0, &err));
+    int Mbest = M0;
     if (err <= tol) {
-        int lo = 4, hi = 32;  // M = 2 * index; lo fails (M = 8 tested below), hi passes
-        double e8 = INFINITY;
-        RBF_TRY(error_at(8, &e8));
-        if (e8 <= tol) {
-            hi = 4;
-            err = e8;
-        } else {
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) / 2;
-                double e = INFINITY;
-                RBF_TRY(error_at(2 * mid, &e));
-                if (e <= tol) {
-                    hi = mid;
-                    err = e;
-                } else {
-                    lo = mid;
-                }
-            }
+        while (Mbest > 8) {
+            double e = INFINITY;
+            RBF_TRY(error_at(Mbest - 2, &e));
+            if (e > tol) break;
+            Mbest -= 2;
+            err = e;
         }
-        Mbest = 2 * hi;
-        if (Mbest == 64) RBF_TRY(error_at(64, &err));
+    } else {
+        while (Mbest < 64 && err > tol) {
+            Mbest += 2;
+            RBF_TRY(error_at(Mbest, &err));
+        }
     }
     p.M = Mbest;
     *out = p;

@@ -71,19 +71,29 @@ __global__ void k_scatter_cols(const float *near, const float *far, const int32_
 }
 
 // Workspace of G right-hand sides at once: leaf and local expansions per
-// column plus FP32 vectors.  G is the largest count within min(64 GB, half of
-// the free device memory), then balanced over the groups of R columns.
+// column plus FP32 vectors.  G = min(R, 16, what fits in min(64 GB, half of the
+// free device memory)), then balanced over the groups of R columns; the
+// workspace is kept and grown only when a later call needs more columns.
 int multi_workspace(rbf_tree *t, rbf_plan *p, int R, int *G_out)
 {
     const size_t per = 2 * (size_t)t->nleaf() * p->mstride * sizeof(float2) +
                        3 * (size_t)t->N * sizeof(float);
-    if (p->mr_G == 0) {
+    const int want = std::min(R, 16);
+    if (p->mr_G < want) {
+        rbf_free(p->mr_V);
+        rbf_free(p->mr_L);
+        rbf_free(p->mr_lam);
+        rbf_free(p->mr_un);
+        rbf_free(p->mr_uf);
+        p->mr_V = p->mr_L = nullptr;
+        p->mr_lam = p->mr_un = p->mr_uf = nullptr;
+        p->mr_G = 0;
         size_t fr = 0, tot = 0;
         RBF_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
         const size_t budget = std::min<size_t>((size_t)64 << 30, fr / 2);
-        int gmax = (int)std::min<size_t>(16, std::max<size_t>(1, budget / per));
         RBF_REQUIRE(per <= budget, "rbf_fmm_matvec: %zu bytes per right-hand side exceed the budget",
                     per);
+        const int gmax = (int)std::min<size_t>((size_t)want, budget / per);
         RBF_TRY(rbf_alloc(&p->mr_V, (size_t)gmax * t->nleaf() * p->mstride));
         // 64-byte tail: bulk copies of the last mode rows round up to 16 bytes
         RBF_TRY(rbf_alloc(&p->mr_L, (size_t)gmax * t->nleaf() * p->mstride + 8));
