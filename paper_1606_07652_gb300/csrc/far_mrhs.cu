@@ -13,14 +13,16 @@
 // with A', B' the phases of the opposite sign (e^{+i xi (x_i - c)}).
 //
 // Each complex product runs as ONE real product whose K dimension stacks six
-// slots per point (P2M) or per mode row (L2P).  With x = hi + lo, hi = tf32(x),
-// lo = tf32(x - hi), the six slots hold
+// k-steps per point (P2M) or per mode row (L2P).  With x = hi + lo,
+// hi = tf32(x), lo = tf32(x - hi), the six k-steps pair
 //     A:  re_hi  im_hi  re_hi  im_hi  re_lo  im_lo
 //     Wr: wr_hi -wi_hi  wr_lo -wi_lo  wr_hi -wi_hi      (output column: real part)
 //     Wi: wi_hi  wr_hi  wi_lo  wr_lo  wi_hi  wr_hi      (output column: imaginary part)
 // so that a column of real parts accumulates A_re W_re - A_im W_im and a
 // column of imaginary parts A_re W_im + A_im W_re, every real product taken as
-// hi*hi + hi*lo + lo*hi (three-term split TF32, FP32-level accuracy).
+// hi*hi + hi*lo + lo*hi (three-term split TF32, FP32-level accuracy).  Only
+// four slots of each operand are stored (A: re_hi im_hi re_lo im_lo; W: its
+// first four); the descriptors of k-steps 2..5 point at the slots they repeat.
 //
 // Tile: 128 rows (TMEM lanes) x 2*NT real columns (NT complex: 16, 32, 48 or
 // 64); K advances 8 points (mode rows) = 48 TF32 values per stage.  Operands
@@ -47,13 +49,19 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kRows = 128;           // tile rows = TMEM lanes
 constexpr int kKS = 8;               // points (P2M) or mode rows (L2P) per stage
-constexpr int kSlots = 6;
-constexpr int kKStage = kSlots * kKS;          // 48 TF32 values of K per stage
-constexpr int kCoreK = kKStage / 4;            // 12 core matrices along K
+constexpr int kSlots = 6;                      // MMA k-steps per stage
+constexpr int kStore = 4;                      // operand slots stored per stage
+constexpr int kKStage = kStore * kKS;          // 32 TF32 values of K stored per stage
+constexpr int kCoreK = kKStage / 4;            // 8 core matrices along K
 constexpr uint32_t kLBO = 128;                 // next core matrix along K
 constexpr uint32_t kSBO = kCoreK * 128;        // next group of 8 rows
-constexpr int kABytes = kRows * kKStage * 4;   // 24576
+constexpr int kABytes = kRows * kKStage * 4;   // 16384
 constexpr long long kWaitCycles = 4000000000LL;
+constexpr uint32_t kSuspendNs = 200000;       // try_wait suspend-time hint
+#ifndef RBF_TC_BACKOFF_NS
+#define RBF_TC_BACKOFF_NS 64
+#endif
+constexpr unsigned kBackoffNs = RBF_TC_BACKOFF_NS;   // sleep after a failed try_wait
 constexpr int kMaxNT = 64;                     // complex columns of a tile
 
 __device__ unsigned int g_tc_status;
@@ -64,18 +72,13 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ uint32_t tf32_bits(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-// x = hi + lo, both TF32
+// x = hi + lo: hi = x rounded to TF32 (nearest, ties away: add half of the 13
+// dropped bits, clear them), lo = x - hi exactly; the MMA reads lo's top 19 bits
+// (truncation, at most 2^-21 |x|), so x is carried to FP32-level accuracy
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
 {
-    hi = __uint_as_float(tf32_bits(x));
-    lo = __uint_as_float(tf32_bits(x - hi));
+    hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+    lo = x - hi;
 }
 
 // shared-memory matrix descriptor: K-major, no swizzle, version 1 (tcgen05)
@@ -101,15 +104,17 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
+// test for the completion of phase `parity`; a thread whose phase is not complete
+// is suspended (up to the hint, in ns) instead of spinning on issue slots
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -182,7 +187,8 @@ __device__ __forceinline__ uint32_t op_off(int r, int s, int q)
     return (uint32_t)((((r >> 3) * kCoreK + 2 * s + q) << 7) + ((r & 7) << 4));
 }
 
-// stores the six slots of a row of the A-side operand (4 consecutive K values)
+// stores the four slots of a row of the A-side operand (4 consecutive K values):
+// re_hi, im_hi, re_lo, im_lo
 __device__ __forceinline__ void put_a(unsigned char *tile, int r, int q, const float *re,
                                       const float *im)
 {
@@ -192,19 +198,17 @@ __device__ __forceinline__ void put_a(unsigned char *tile, int r, int q, const f
         split_tf32(re[e], rh[e], rl[e]);
         split_tf32(im[e], ih[e], il[e]);
     }
-    const float4 RH = make_float4(rh[0], rh[1], rh[2], rh[3]);
-    const float4 IH = make_float4(ih[0], ih[1], ih[2], ih[3]);
-    *reinterpret_cast<float4 *>(tile + op_off(r, 0, q)) = RH;
-    *reinterpret_cast<float4 *>(tile + op_off(r, 1, q)) = IH;
-    *reinterpret_cast<float4 *>(tile + op_off(r, 2, q)) = RH;
-    *reinterpret_cast<float4 *>(tile + op_off(r, 3, q)) = IH;
-    *reinterpret_cast<float4 *>(tile + op_off(r, 4, q)) = make_float4(rl[0], rl[1], rl[2], rl[3]);
-    *reinterpret_cast<float4 *>(tile + op_off(r, 5, q)) = make_float4(il[0], il[1], il[2], il[3]);
+    *reinterpret_cast<float4 *>(tile + op_off(r, 0, q)) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+    *reinterpret_cast<float4 *>(tile + op_off(r, 1, q)) = make_float4(ih[0], ih[1], ih[2], ih[3]);
+    *reinterpret_cast<float4 *>(tile + op_off(r, 2, q)) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+    *reinterpret_cast<float4 *>(tile + op_off(r, 3, q)) = make_float4(il[0], il[1], il[2], il[3]);
 }
 
-// stores the real-part row j and the imaginary-part row NT + j of the W-side operand
-__device__ __forceinline__ void put_w(unsigned char *tile, int j, int NT, int q, const float *wr,
-                                      const float *wi)
+// stores one row of the W-side operand for complex column j: half 0 = the
+// real-part row j (wr_hi, -wi_hi, wr_lo, -wi_lo), half 1 = the imaginary-part
+// row NT + j (wi_hi, wr_hi, wi_lo, wr_lo)
+__device__ __forceinline__ void put_w_half(unsigned char *tile, int j, int NT, int q, int half,
+                                           const float *wr, const float *wi)
 {
     float rh[4], rl[4], ih[4], il[4];
 #pragma unroll
@@ -212,25 +216,18 @@ __device__ __forceinline__ void put_w(unsigned char *tile, int j, int NT, int q,
         split_tf32(wr[e], rh[e], rl[e]);
         split_tf32(wi[e], ih[e], il[e]);
     }
-    const float4 RH = make_float4(rh[0], rh[1], rh[2], rh[3]);
-    const float4 RL = make_float4(rl[0], rl[1], rl[2], rl[3]);
-    const float4 IH = make_float4(ih[0], ih[1], ih[2], ih[3]);
-    const float4 IL = make_float4(il[0], il[1], il[2], il[3]);
-    const float4 NIH = make_float4(-ih[0], -ih[1], -ih[2], -ih[3]);
-    const float4 NIL = make_float4(-il[0], -il[1], -il[2], -il[3]);
-    *reinterpret_cast<float4 *>(tile + op_off(j, 0, q)) = RH;
-    *reinterpret_cast<float4 *>(tile + op_off(j, 1, q)) = NIH;
-    *reinterpret_cast<float4 *>(tile + op_off(j, 2, q)) = RL;
-    *reinterpret_cast<float4 *>(tile + op_off(j, 3, q)) = NIL;
-    *reinterpret_cast<float4 *>(tile + op_off(j, 4, q)) = RH;
-    *reinterpret_cast<float4 *>(tile + op_off(j, 5, q)) = NIH;
-    const int n = NT + j;
-    *reinterpret_cast<float4 *>(tile + op_off(n, 0, q)) = IH;
-    *reinterpret_cast<float4 *>(tile + op_off(n, 1, q)) = RH;
-    *reinterpret_cast<float4 *>(tile + op_off(n, 2, q)) = IL;
-    *reinterpret_cast<float4 *>(tile + op_off(n, 3, q)) = RL;
-    *reinterpret_cast<float4 *>(tile + op_off(n, 4, q)) = IH;
-    *reinterpret_cast<float4 *>(tile + op_off(n, 5, q)) = RH;
+    if (half == 0) {
+        *reinterpret_cast<float4 *>(tile + op_off(j, 0, q)) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+        *reinterpret_cast<float4 *>(tile + op_off(j, 1, q)) = make_float4(-ih[0], -ih[1], -ih[2], -ih[3]);
+        *reinterpret_cast<float4 *>(tile + op_off(j, 2, q)) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+        *reinterpret_cast<float4 *>(tile + op_off(j, 3, q)) = make_float4(-il[0], -il[1], -il[2], -il[3]);
+    } else {
+        const int n = NT + j;
+        *reinterpret_cast<float4 *>(tile + op_off(n, 0, q)) = make_float4(ih[0], ih[1], ih[2], ih[3]);
+        *reinterpret_cast<float4 *>(tile + op_off(n, 1, q)) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+        *reinterpret_cast<float4 *>(tile + op_off(n, 2, q)) = make_float4(il[0], il[1], il[2], il[3]);
+        *reinterpret_cast<float4 *>(tile + op_off(n, 3, q)) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+    }
 }
 
 __device__ __forceinline__ void decode_key(uint64_t key, int d, int l, int *k)
@@ -238,17 +235,6 @@ __device__ __forceinline__ void decode_key(uint64_t key, int d, int l, int *k)
     for (int t = 0; t < d; ++t) k[t] = 0;
     for (int b = 0; b < l; ++b)
         for (int t = 0; t < d; ++t) k[t] |= (int)((key >> (b * d + t)) & 1u) << b;
-}
-
-// prod_{t<d-2} E_t[k_t] of the prefix Q = (k0, .., k_{d-3}) of a mode row (d >= 3)
-__device__ __forceinline__ float2 prefix_phase(const float2 *E, int Q, int d, int n0, int n1)
-{
-    float2 v = make_float2(1.0f, 0.0f);
-    for (int t = d - 3; t >= 1; --t) {
-        v = cmul(v, E[n0 + (t - 1) * n1 + Q % n1]);
-        Q /= n1;
-    }
-    return cmul(v, E[Q]);
 }
 
 struct TcArgs {
@@ -303,10 +289,11 @@ constexpr int kEpiWarp0 = kProdWarps + 1;              // warps 9..16: accumulat
 constexpr int kEpiWarps = 8;
 constexpr int kCopyWarp = kEpiWarp0 + kEpiWarps;       // warp 17: bulk copies
 constexpr int kTcThreads = 32 * (kCopyWarp + 1);       // 576
-constexpr int kP2MStages = 3, kL2PStages = 2, kMaxStages = 3;
+constexpr int kP2MStages = 4, kL2PStages = 3, kMaxStages = 4;
 constexpr int kRing = 8;                               // copy-slot barriers
-constexpr int kRingE = 8, kRingL = 4;                  // copy slots of P2M, L2P
-constexpr int kBarProd = 1, kBarEpi = 2;               // named barriers (0 = __syncthreads)
+constexpr int kRingE = 8, kRingL = 6;                  // copy slots of P2M, L2P
+// named barriers (0 = __syncthreads): all producers, epilogue, P2M producer groups
+constexpr int kBarProd = 1, kBarEpi = 2, kBarGrp0 = 3;
 constexpr int kPF = 48;   // prefixes per 128-row tile: 128 / n1 + 2 <= 48 for n1 >= 3
 
 // Accumulation blocks: the MMAs of kBlock consecutive stages of a work item
@@ -345,10 +332,11 @@ __device__ __forceinline__ Sync sync_at(void *end)
     return y;
 }
 
-__device__ __forceinline__ void sync_init(const Sync &y)
+// parts: producer warps that arrive per stage (and per copy slot)
+__device__ __forceinline__ void sync_init(const Sync &y, int parts)
 {
     for (int k = 0; k < kMaxStages; ++k) {
-        mbar_init(smem_u32(&y.full[k]), kProdWarps);
+        mbar_init(smem_u32(&y.full[k]), parts);
         mbar_init(smem_u32(&y.empty[k]), 1);
     }
     for (int k = 0; k < 2; ++k) {
@@ -357,7 +345,7 @@ __device__ __forceinline__ void sync_init(const Sync &y)
     }
     for (int k = 0; k < kRing; ++k) {
         mbar_init(smem_u32(&y.rfull[k]), 1);
-        mbar_init(smem_u32(&y.rempty[k]), kProdWarps);
+        mbar_init(smem_u32(&y.rempty[k]), parts);
     }
     *y.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -385,6 +373,7 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
             *abort = 1;
             return false;
         }
+        __nanosleep(kBackoffNs);   // leave the issue slots to the warps with work
     }
     return true;
 }
@@ -435,9 +424,11 @@ __device__ __forceinline__ void mma_item(const Sync &y, int nch, int &gc, int &g
         const uint32_t a0 = smem_u32(smem + s * sbytes), b0 = a0 + (uint32_t)kABytes;
         const uint32_t d = tmem + (uint32_t)(buf * 2 * NT);
         const bool fresh = lc % kBlock == 0;
+        // stored slots of the six k-steps: A (hi, hi, hi, hi, lo, lo), W (hi, hi, lo, lo, hi, hi)
+        constexpr uint32_t sa[kSlots] = {0, 1, 0, 1, 2, 3}, sw[kSlots] = {0, 1, 2, 3, 0, 1};
 #pragma unroll
         for (int k = 0; k < kSlots; ++k)
-            mma_tf32(d, smem_desc(a0 + 256u * k), smem_desc(b0 + 256u * k), idesc,
+            mma_tf32(d, smem_desc(a0 + 256u * sa[k]), smem_desc(b0 + 256u * sw[k]), idesc,
                      (fresh && k == 0) ? 0u : 1u);
         mma_commit(smem_u32(&y.empty[s]));
         if (block_end(lc, nch)) {
@@ -527,12 +518,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_p2m_tc(const TcArgs a, const 
     const int eslot = kKS * rowpadE, lslot = kKS * gpad;
     float2 *Er = reinterpret_cast<float2 *>(smem + S * sbytes);       // [kRingE][kKS][rowpadE]
     float *Lr = reinterpret_cast<float *>(Er + kRingE * eslot);        // [kRingE][kKS][gpad]
-    float2 *PF = reinterpret_cast<float2 *>(Lr + kRingE * lslot);      // [2][kKS][kPF]
-    const Sync y = sync_at(PF + 2 * kKS * kPF);
+    float2 *PF = reinterpret_cast<float2 *>(Lr + kRingE * lslot);      // [2 groups][2][kKS][kPF]
+    int *pfo = reinterpret_cast<int *>(PF + 4 * kKS * kPF);            // [2][kPF][RBF_MAX_DIM]
+    const Sync y = sync_at(pfo + 2 * kPF * RBF_MAX_DIM);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntot = a.ncol * a.G;
-    if (tid == 0) sync_init(y);
+    if (tid == 0) sync_init(y, kProdWarps / 2);
     __syncwarp();
     if (warp == 0) tmem_alloc(smem_u32(y.tslot), a.tcols);
     tc_fence_before();
@@ -542,58 +534,82 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_p2m_tc(const TcArgs a, const 
 
     int gc = 0, gb = 0;          // stages and blocks of all items handled so far (per role)
     int last = -1, issued = 0;   // last committed stage (MMA lane), stages copied (copy lane)
-    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    int nit = 0;                 // items handled by this CTA
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x, ++nit) {
         const int ct = w % ntile2, rtile = (w / ntile2) % ntile1, leaf = w / (ntile2 * ntile1);
         const int row0 = rtile * kRows, n0c = ct * NT;
         const int64_t p0 = a.leaf_off[leaf];
         const int np = a.leaf_off[leaf + 1] - (int)p0;
         const int nch = (np + kKS - 1) / kKS;
         if (warp < kProdWarps) {
-            // ---- producers
-            const int rt = tid & (kRows - 1), qa = tid >> 7;
-            const int row = row0 + rt;
-            const bool row_ok = row < a.nrow;
+            // ---- producers: two groups of four warps build alternate stages, so
+            // the latency chains of two stages overlap
+            const int grp = warp >> 2, gt = tid & 127;
             const int rlast = min(row0 + kRows, a.nrow) - 1;
             const int qbase = a.d >= 3 ? row0 / a.n1 : 0;
             const int npf = a.d >= 3 ? rlast / a.n1 - qbase + 1 : 0;
+            const int row = row0 + gt;
+            const bool row_ok = row < a.nrow;
             const int qloc = a.d >= 3 && row_ok ? row / a.n1 - qbase : 0;
             const int oe = a.d >= 3 ? a.n0 + (a.d - 3) * a.n1 + (row_ok ? row % a.n1 : 0)
                                     : (row_ok ? row : 0);
             const int ocol = a.d == 1 ? 0 : a.n0 + (a.d - 2) * a.n1;
-            for (int lc = 0; lc < nch; ++lc, ++gc) {
-                const int s = gc % S, k = gc % kRingE;
-                if (gc >= S && !*y.abort) (void)wait_or_abort(&y.empty[s], ((gc - S) / S) & 1, y.abort);
-                if (!*y.abort) (void)wait_or_abort(&y.rfull[k], (uint32_t)(gc / kRingE) & 1u, y.abort);
+            // table offsets of the tile's prefixes, one buffer per item parity (every
+            // producer finished the item before last at the previous item's barrier)
+            int *pfi = pfo + (nit & 1) * kPF * RBF_MAX_DIM;
+            for (int q = tid; q < npf; q += kThreads) {
+                int Q = qbase + q;
+                for (int t = a.d - 3; t >= 1; --t) {
+                    pfi[q * RBF_MAX_DIM + t] = a.n0 + (t - 1) * a.n1 + Q % a.n1;
+                    Q /= a.n1;
+                }
+                pfi[q * RBF_MAX_DIM] = Q;
+            }
+            named_bar(kBarProd, kThreads);
+            for (int lc = grp; lc < nch; lc += 2) {
+                const int gcc = gc + lc;
+                const int s = gcc % S, k = gcc % kRingE;
+                if (gcc >= S && !*y.abort) (void)wait_or_abort(&y.empty[s], ((gcc - S) / S) & 1, y.abort);
+                if (!*y.abort) (void)wait_or_abort(&y.rfull[k], (uint32_t)(gcc / kRingE) & 1u, y.abort);
                 const int cnt = min(kKS, np - lc * kKS);
                 const float2 *Ec = Er + k * eslot;
                 const float *Lc = Lr + k * lslot;
-                float2 *PFc = PF + (gc & 1) * kKS * kPF;
+                float2 *PFc = PF + (grp * 2 + ((lc >> 1) & 1)) * kKS * kPF;
                 if (!*y.abort)
-                    for (int idx = tid; idx < kKS * npf; idx += kThreads) {
+                    for (int idx = gt; idx < kKS * npf; idx += 128) {
                         const int p = idx / npf, q = idx - p * npf;
-                        PFc[p * kPF + q] = p < cnt ? prefix_phase(Ec + p * rowpadE, qbase + q, a.d,
-                                                                  a.n0, a.n1)
-                                                   : make_float2(0.0f, 0.0f);
+                        float2 v = make_float2(0.0f, 0.0f);
+                        if (p < cnt) {
+                            const float2 *Epp = Ec + p * rowpadE;
+                            const int *o = pfi + q * RBF_MAX_DIM;
+                            v = Epp[o[0]];
+                            for (int t = 1; t <= a.d - 3; ++t) v = cmul(v, Epp[o[t]]);
+                        }
+                        PFc[p * kPF + q] = v;
                     }
-                named_bar(kBarProd, kThreads);
+                named_bar(kBarGrp0 + grp, 128);
                 if (!*y.abort) {
                     unsigned char *tile = smem + s * sbytes;
-                    float re[4], im[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int p = 4 * qa + e;
-                        float2 v = make_float2(0.0f, 0.0f);
-                        if (row_ok && p < cnt) {
-                            if (a.d >= 3) v = cmul(PFc[p * kPF + qloc], Ec[p * rowpadE + oe]);
-                            else if (a.d == 2) v = Ec[p * rowpadE + oe];
-                            else v = make_float2(1.0f, 0.0f);
+                    for (int qa = 0; qa < 2; ++qa) {
+                        float re[4], im[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int p = 4 * qa + e;
+                            float2 v = make_float2(0.0f, 0.0f);
+                            if (row_ok && p < cnt) {
+                                if (a.d >= 3) v = cmul(PFc[p * kPF + qloc], Ec[p * rowpadE + oe]);
+                                else if (a.d == 2) v = Ec[p * rowpadE + oe];
+                                else v = make_float2(1.0f, 0.0f);
+                            }
+                            re[e] = v.x;
+                            im[e] = v.y;
                         }
-                        re[e] = v.x;
-                        im[e] = v.y;
+                        put_a(tile, gt, qa, re, im);
                     }
-                    put_a(tile, rt, qa, re, im);
-                    for (int idx = tid; idx < 2 * NT; idx += kThreads) {
-                        const int j = idx >> 1, qq = idx & 1;
+                    // W rows: one (column, point quad, half) per item
+                    for (int idx = gt; idx < 4 * NT; idx += 128) {
+                        const int j = idx >> 2, qq = (idx >> 1) & 1, half = idx & 1;
                         const int n = n0c + j;
                         float wr[4] = {0, 0, 0, 0}, wi[4] = {0, 0, 0, 0};
                         if (n < ntot) {
@@ -609,7 +625,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_p2m_tc(const TcArgs a, const 
                                 }
                             }
                         }
-                        put_w(tile + kABytes, j, NT, qq, wr, wi);
+                        put_w_half(tile + kABytes, j, NT, qq, half, wr, wi);
                     }
                     fence_async_smem();
                 }
@@ -619,6 +635,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_p2m_tc(const TcArgs a, const 
                     mbar_arrive(smem_u32(&y.rempty[k]));
                 }
             }
+            gc += nch;
         } else if (warp == kMmaWarp) {
             if (lane == 0) mma_item<S>(y, nch, gc, gb, last, smem, sbytes, tmem, a.idesc, NT);
         } else if (warp == kCopyWarp) {
@@ -706,7 +723,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_l2p_tc(const TcArgs a, const 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ncolt = Rg * a.ncol;        // columns of the tile
     const int nch = (a.nrow + kKS - 1) / kKS;
-    if (tid == 0) sync_init(y);
+    if (tid == 0) sync_init(y, kProdWarps / 2);
     __syncwarp();
     if (warp == 0) tmem_alloc(smem_u32(y.tslot), a.tcols);
     tc_fence_before();
@@ -736,69 +753,112 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_l2p_tc(const TcArgs a, const 
                                               : make_float2(0.0f, 0.0f);
             }
             named_bar(kBarProd, kThreads);
-            const int pa = tid & (kRows - 1), qa = tid >> 7;
-            const float2 *Ep = E + pa * a.rowpad;
-            const int jw = tid >> 1, qw = tid & 1;
-            const int rlw = jw / a.ncol, colw = jw - rlw * a.ncol;
-            const bool w_on = jw < NT;
-            const bool w_val = jw < ncolt && rlw < rgv;
+            // two groups of four warps take alternate stages; thread gt of a group
+            // owns point gt (all 8 mode rows of a stage) and up to two W rows
+            const int grp = warp >> 2, gt = tid & 127;
+            const float2 *Ep = E + gt * a.rowpad;
             const float2 *Elast = Ep + (a.d >= 3 ? a.n0 + (a.d - 3) * a.n1 : 0);
-            for (int lc = 0; lc < nch; ++lc, ++gc) {
-                const int s = gc % S, k = gc % kRingL;
-                if (gc >= S && !*y.abort) (void)wait_or_abort(&y.empty[s], ((gc - S) / S) & 1, y.abort);
-                unsigned char *tile = smem + s * sbytes;
-                if (!*y.abort && w_on) {
-                    float wr[4] = {0, 0, 0, 0}, wi[4] = {0, 0, 0, 0};
-                    if (w_val && wait_or_abort(&y.rfull[k], (uint32_t)(gc / kRingL) & 1u, y.abort)) {
-                        const float2 *sl = ring + k * slot_c + rlw * kKS * a.ncol + colw;
+            // mode row = (prefix digits dg, k_{d-2} = kl), advanced row by row
+            int dg[RBF_MAX_DIM - 2] = {0, 0, 0, 0};
+            int kl = 0;
+            float2 pf = make_float2(1.0f, 0.0f);
+            // (fixed-size unrolled loops keep the digits in registers)
+            auto prefix_from_digits = [&]() {
+                float2 v = Ep[dg[0]];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int rr = 4 * qw + e;
-                            if (lc * kKS + rr < a.nrow) {
-                                const float2 v = sl[rr * a.ncol];
-                                wr[e] = v.x;
-                                wi[e] = v.y;
-                            }
+                for (int t = 1; t < RBF_MAX_DIM - 2; ++t)
+                    if (t <= a.d - 3) v = cmul(v, Ep[a.n0 + (t - 1) * a.n1 + dg[t]]);
+                return v;
+            };
+            auto advance = [&](int rows) {   // kl += rows with carries into the prefix
+                bool moved = false;
+                kl += rows;
+                while (kl >= a.n1) {
+                    kl -= a.n1;
+                    moved = true;
+                    bool carry = true;
+#pragma unroll
+                    for (int t = RBF_MAX_DIM - 3; t >= 1; --t) {
+                        if (t <= a.d - 3 && carry) {
+                            if (++dg[t] == a.n1) dg[t] = 0;
+                            else carry = false;
                         }
                     }
-                    put_w(tile + kABytes, jw, NT, qw, wr, wi);
+                    if (carry) ++dg[0];
                 }
+                return moved;
+            };
+            if (a.d >= 3) {
+                int Q = (grp * kKS) / a.n1;
+                kl = grp * kKS - Q * a.n1;
+#pragma unroll
+                for (int t = RBF_MAX_DIM - 3; t >= 1; --t) {
+                    if (t <= a.d - 3) {
+                        dg[t] = Q % a.n1;
+                        Q /= a.n1;
+                    }
+                }
+                dg[0] = Q;
+                if (grp * kKS < a.nrow) pf = prefix_from_digits();
+            }
+            for (int lc = grp; lc < nch; lc += 2) {
+                const int gcc = gc + lc;
+                const int s = gcc % S, k = gcc % kRingL;
+                if (gcc >= S && !*y.abort) (void)wait_or_abort(&y.empty[s], ((gcc - S) / S) & 1, y.abort);
+                unsigned char *tile = smem + s * sbytes;
+                const bool ready = !*y.abort && wait_or_abort(&y.rfull[k], (uint32_t)(gcc / kRingL) & 1u, y.abort);
+                if (ready)
+                    for (int idx = gt; idx < 4 * NT; idx += 128) {
+                        const int jw = idx >> 2, qw = (idx >> 1) & 1, hw = idx & 1;
+                        const int rlw = jw / a.ncol, colw = jw - rlw * a.ncol;
+                        float wr[4] = {0, 0, 0, 0}, wi[4] = {0, 0, 0, 0};
+                        if (jw < ncolt && rlw < rgv) {
+                            const float2 *sl = ring + k * slot_c + rlw * kKS * a.ncol + colw;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int rr = 4 * qw + e;
+                                if (lc * kKS + rr < a.nrow) {
+                                    const float2 v = sl[rr * a.ncol];
+                                    wr[e] = v.x;
+                                    wi[e] = v.y;
+                                }
+                            }
+                        }
+                        put_w_half(tile + kABytes, jw, NT, qw, hw, wr, wi);
+                    }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&y.rempty[k]));
                 if (!*y.abort) {
-                    // row = (prefix Q, k_{d-2}): A'_i[row] = PF_i(Q) E_{d-2}[i][k_{d-2}],
-                    // the prefix product formed again only when Q changes
-                    float re[4], im[4];
-                    const int rw0 = lc * kKS + 4 * qa;
-                    int Q = a.d >= 3 ? rw0 / a.n1 : 0, kl = a.d >= 3 ? rw0 - Q * a.n1 : 0;
-                    float2 pf = a.d >= 3 && rw0 < a.nrow ? prefix_phase(Ep, Q, a.d, a.n0, a.n1)
-                                                          : make_float2(1.0f, 0.0f);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int rw = rw0 + e;
-                        float2 v = make_float2(0.0f, 0.0f);
-                        if (rw < a.nrow) {
-                            if (a.d >= 3) {
-                                v = cmul(pf, Elast[kl]);
-                                if (++kl == a.n1 && rw + 1 < a.nrow) {
-                                    kl = 0;
-                                    pf = prefix_phase(Ep, ++Q, a.d, a.n0, a.n1);
+                    for (int qa = 0; qa < 2; ++qa) {
+                        float re[4], im[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int rw = lc * kKS + 4 * qa + e;
+                            float2 v = make_float2(0.0f, 0.0f);
+                            if (rw < a.nrow) {
+                                if (a.d >= 3) {
+                                    v = cmul(pf, Elast[kl]);
+                                    if (advance(1) && rw + 1 < a.nrow) pf = prefix_from_digits();
+                                } else if (a.d == 2) {
+                                    v = Ep[rw];
+                                } else {
+                                    v = make_float2(1.0f, 0.0f);
                                 }
-                            } else if (a.d == 2) {
-                                v = Ep[rw];
-                            } else {
-                                v = make_float2(1.0f, 0.0f);
                             }
+                            re[e] = v.x;
+                            im[e] = v.y;
                         }
-                        re[e] = v.x;
-                        im[e] = v.y;
+                        put_a(tile, gt, qa, re, im);
                     }
-                    put_a(tile, pa, qa, re, im);
                     fence_async_smem();
                 }
+                // skip the other group's stage
+                if (a.d >= 3 && advance(kKS) && (lc + 2) * kKS < a.nrow) pf = prefix_from_digits();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&y.full[s]));
             }
+            gc += nch;
         } else if (warp == kMmaWarp) {
             if (lane == 0) mma_item<S>(y, nch, gc, gb, last, smem, sbytes, tmem, a.idesc, NT);
         } else if (warp == kCopyWarp) {
@@ -935,7 +995,8 @@ void p2m_shape(const rbf_tree *t, const rbf_plan *p, int G, int *nth, size_t *sm
     const int gpad = 16;   // coefficient columns of the point-major copy
     *smem = stage_bytes(16 * best_c, kP2MStages) +
             (size_t)kRingE * kKS * (rowpad_even(t, p) * sizeof(float2) + gpad * sizeof(float)) +
-            (size_t)2 * kKS * kPF * sizeof(float2) + kSyncBytes;
+            (size_t)4 * kKS * kPF * sizeof(float2) + (size_t)2 * kPF * RBF_MAX_DIM * sizeof(int) +
+            kSyncBytes;
 }
 
 // L2P tile: right-hand sides per tile, complex columns (16 NTH) and shared memory
