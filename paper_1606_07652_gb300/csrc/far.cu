@@ -762,7 +762,8 @@ __global__ void __launch_bounds__(256) k_m2l_full(int d, int M, int n1, int64_t 
     int nbox = 1;
     for (int t = 0; t < d; ++t) nbox *= S;
     C *grid = reinterpret_cast<C *>(smem_raw);                          // [nbox][MC]
-    int *kid = reinterpret_cast<int *>(grid + (int64_t)nbox * MC);      // [d][MC] frequency index
+    C *rph = grid + (int64_t)nbox * MC;                                  // [d][S][MC] root phases
+    int *kid = reinterpret_cast<int *>(rph + d * S * MC);               // [d][MC] frequency index
     uint32_t *lc = reinterpret_cast<uint32_t *>(kid + d * MC);          // [nleaf] packed coordinates
     const int64_t m0 = (int64_t)blockIdx.x * MC;
     const int mc = (int)min((int64_t)MC, nmode - m0);
@@ -794,10 +795,30 @@ __global__ void __launch_bounds__(256) k_m2l_full(int d, int M, int n1, int64_t 
     }
     for (int q = threadIdx.x; q < nbox * MC; q += blockDim.x) grid[q] = C{(R)0, (R)0};
     __syncthreads();
-    for (int q = threadIdx.x; q < nleaf * MC; q += blockDim.x) {
-        const int l = q / MC, mm = q - l * MC;
-        if (mm >= mc) continue;
-        grid[(int64_t)lc[l] * MC + mm] = VD[(int64_t)l * ms + m0 + mm];
+    // e^{i xi_k (c_t(k) - c_0,t)} per dimension, leaf coordinate and mode of the CTA
+    for (int q = threadIdx.x; q < d * S * MC; q += blockDim.x) {
+        const int t = q / (S * MC), r = q - t * S * MC, kt = r / MC, mm = r - kt * MC;
+        rph[q] = root_ph[((int64_t)t * S + kt) * n1 + kid[t * MC + mm]];
+    }
+    // leaf expansions -> grid, eight loads in flight per thread
+    {
+        constexpr int U = 8;
+        const int nq = nleaf * MC;
+        for (int q0 = threadIdx.x; q0 < nq; q0 += U * blockDim.x) {
+            C v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u * blockDim.x;
+                const int l = q / MC, mm = q - l * MC;
+                v[u] = (q < nq && mm < mc) ? VD[(int64_t)l * ms + m0 + mm] : C{(R)0, (R)0};
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u * blockDim.x;
+                const int l = q / MC, mm = q - l * MC;
+                if (q < nq && mm < mc) grid[(int64_t)lc[l] * MC + mm] = v[u];
+            }
+        }
     }
     __syncthreads();
     int stride = 1;
@@ -829,10 +850,10 @@ __global__ void __launch_bounds__(256) k_m2l_full(int d, int M, int n1, int64_t 
         if (mm >= mc) continue;
         const uint32_t w = lc[l];
         const int64_t m = m0 + mm;
-        C ph = root_ph[(int64_t)(w & (S - 1)) * n1 + kid[mm]];
+        C ph = rph[(int)(w & (S - 1)) * MC + mm];
         for (int t = 1; t < d; ++t) {
             const int kt = (int)((w >> (SB * t)) & (S - 1));
-            ph = cmul(ph, root_ph[((int64_t)t * S + kt) * n1 + kid[t * MC + mm]]);
+            ph = cmul(ph, rph[(t * S + kt) * MC + mm]);
         }
         const C r = cmul(ph, V0[m]);
         const C sa = grid[(int64_t)w * MC + mm];
@@ -972,8 +993,8 @@ int rbf_run_m2l(rbf_tree *t, const rbf_plan *p, const cplx<R> *VD, cplx<R> *L, c
         const int S = 1 << D;
         const int64_t nbox = (int64_t)1 << (d * D);
         const int MC = (int)std::max<int64_t>(1, std::min<int64_t>(16, (96 * 1024) / (nbox * (int64_t)sizeof(C))));
-        const size_t smem = (size_t)nbox * MC * sizeof(C) + (size_t)d * MC * sizeof(int) +
-                            (size_t)t->nleaf() * sizeof(uint32_t);
+        const size_t smem = (size_t)nbox * MC * sizeof(C) + (size_t)d * S * MC * sizeof(C) +
+                            (size_t)d * MC * sizeof(int) + (size_t)t->nleaf() * sizeof(uint32_t);
         const int nblk = ceil_div(p->nmode, MC);
 #define RBF_M2L_FULL(SS)                                                                          \
     do {                                                                                          \
