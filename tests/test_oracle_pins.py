@@ -7,6 +7,7 @@ exact translation identities, brute force on tiny inputs, and the far-field
 error bound of the scaled Lemma (Eq. (33)).
 """
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -394,3 +395,104 @@ def test_bf16_rounding_by_hand():
     from oracle.solver import bf16_round
     v = bf16_round(np.array([1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -7, -2.5]))
     assert v.tolist() == [1.0, 1.0 + 2 ** -6, 1.0 + 2 ** -7, -2.5]
+
+
+# ------------------------------------------------------------- T-LAG -----
+def _golden(name):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    rows = []
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(v) for v in line.split()])
+    return rows
+
+
+def test_lagrange_basis_reproduces_paper_error_table():
+    """The Lagrange basis of the nested-grid oracle, on the paper's setting (K
+    equispaced nodes on [-pi, pi], targets xi/2, |x| <= 1), reproduces the
+    printed error table within 1% (K = 8, 11, 12 to every printed digit).  A
+    basis with swapped indices, a missing factor or a wrong target fails."""
+    from oracle import nested as ON
+    for K, err in _golden("lagrange_halfwave_error.txt"):
+        got = ON.lagrange_halfwave_error(int(K))
+        assert abs(got / err - 1.0) < 0.01, (K, got, err)
+        if int(K) in (8, 11, 12):
+            assert float(f"{got:.4e}") == pytest.approx(err, rel=1e-4), (K, got, err)
+
+
+def test_interp_matrix_exact_on_polynomials_and_nodes():
+    """The local K-point stencil matrix reproduces every polynomial of degree < K
+    at the half-node targets (closed form), is the identity selection on even
+    parent nodes, and maps the symmetric grid onto itself mirrored."""
+    from oracle import nested as ON
+    for M, K in ((16, 8), (32, 8), (24, 12), (20, 4)):
+        P = ON.interp_matrix(M, K)
+        j = np.arange(-M // 2, M // 2 + 1, dtype=np.float64)
+        for deg in range(K):
+            assert np.allclose(P @ (j ** deg), (j / 2.0) ** deg, rtol=1e-12, atol=1e-9 * (M ** deg))
+        for kp in range(0, M + 1):
+            k = kp - M // 2
+            if k % 2 == 0:
+                row = np.zeros(M + 1)
+                row[k // 2 + M // 2] = 1.0
+                assert np.array_equal(P[kp], row)
+        assert np.allclose(P[::-1, ::-1], P, rtol=0, atol=1e-15)
+
+
+def test_nested_depth2_equals_shared_grid():
+    """With D = 2 only level 2 couples, and its grid and coefficients are those of
+    the shared grid: the nested product equals the shared-grid product."""
+    from oracle import nested as ON
+    rng = np.random.default_rng(3)
+    X = rng.random((600, 2))
+    lam = rng.standard_normal(600)
+    T = O.tree(X, np.zeros(2), 1.0, 2)
+    wcs = ON.coeffs_levels(O.IMQ, 2.0, 2, 16, 4.0, 4.5, 1.0, 2)
+    wc = O.coeffs_sampled(O.IMQ, 2.0, 2, 16, 4.0, 4.5, 1.0)
+    assert np.array_equal(wcs[2], wc)
+    assert rel(ON.fmm(T, lam, O.IMQ, 2.0, wcs, 16, 4.0, 8), O.fmm(T, lam, O.IMQ, 2.0, wc, 16, 4.0)) < 1e-14
+
+
+@pytest.mark.parametrize("d,N,D,kernel,eps,M,K", [
+    (1, 120, 4, O.IMQ, 2.0, 16, 8),
+    (2, 150, 3, O.IMQ, 2.0, 16, 8),
+    (2, 120, 4, O.GAUSSIAN, 3.0, 16, 6),
+    (3, 90, 3, O.IMQ, 2.0, 8, 4),
+])
+def test_nested_fmm_equals_pairwise_chains(d, N, D, kernel, eps, M, K):
+    """The nested FMM (box expansions, M2M by interpolation, IL_l coupling, L2L by
+    anterpolation) equals the pair-by-pair sum built from one-dimensional phase
+    chains, with pairs classified from their box coordinates."""
+    from oracle import nested as ON
+    rng = np.random.default_rng(7 * N + d)
+    X = rng.random((N, d))
+    lam = rng.standard_normal(N)
+    T = O.tree(X, np.zeros(d), 1.0, D)
+    wcs = ON.coeffs_levels(kernel, eps, d, M, 4.0, 4.5, 1.0, D)
+    u = ON.fmm(T, lam, kernel, eps, wcs, M, 4.0, K)
+    up = ON.fmm_pairwise(X, lam, np.zeros(d), 1.0, D, kernel, eps, wcs, M, 4.0, K)
+    assert rel(u, up) < 1e-13
+
+
+def test_nested_fmm_converges_to_level_kernels():
+    """As K grows the interpolated phases become exact, and the nested product
+    tends to near Phi + far K_l (each far pair with the band-limited kernel of
+    the level that couples it); against the direct sum the error is bounded by
+    max |K_l - Phi| * sum |lambda| plus the interpolation error."""
+    from oracle import nested as ON
+    d, N, D, M, eps = 2, 900, 4, 24, 2.0
+    rng = np.random.default_rng(21)
+    X = rng.random((N, d))
+    lam = rng.standard_normal(N)
+    T = O.tree(X, np.zeros(d), 1.0, D)
+    wcs = ON.coeffs_levels(O.IMQ, eps, d, M, 4.0, 4.5, 1.0, D)
+    ud = O.direct(X, lam, O.IMQ, eps)
+    kerr = ON.kernel_levels_error(O.IMQ, eps, d, M, 4.0, wcs, 1.0, D)
+    errs = []
+    for K in (4, 8, 12):
+        u = ON.fmm(T, lam, O.IMQ, eps, wcs, M, 4.0, K)
+        errs.append(np.max(np.abs(u - ud)))
+    assert errs[0] > errs[1] >= errs[2] * 0.5
+    assert errs[2] <= 1.05 * kerr * np.sum(np.abs(lam))
