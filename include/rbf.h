@@ -72,12 +72,29 @@ typedef enum { RBF_FP64 = 0, RBF_FP32 = 1 } rbf_precision;
  *               |t| <= side and falls to ~0 at |t| = L - side.
  *  csample      1: C(xi) from samples of Phi on the lattice h Z^d, h = L/M
  *               (Eq. (M2Loperator), the paper's kernel-independent route);
- *               0: closed-form Gaussian transform (validation, Gaussian only). */
+ *               0: closed-form Gaussian transform (validation, Gaussian only).
+ *  grid         RBF_GRID_SHARED (0): one frequency grid on every level; M2M and
+ *               L2L are exact diagonal shifts (interpolation P = I in Eqs. (43)
+ *               and (48)).
+ *               RBF_GRID_NESTED (1): the scale-invariant grids of Sec. 4.1.1:
+ *               the same M on every level, xi_{l-1} = xi_l / 2 (level l uses
+ *               period L * 2^(2-l) and coefficients sampled at that scale,
+ *               flat taper radius side * 2^(2-l)); M2M interpolates and L2L
+ *               anterpolates in xi with local Lagrange stencils (Eqs. (43),
+ *               (47), (48), (51)).  Needs d <= 3, csample = 1,
+ *               window_alpha > 0 and M >= 2 lagrange_K; single right-hand-side
+ *               kernels only (several columns run one after another).
+ *  lagrange_K   points of the Lagrange stencil of the nested grids (even,
+ *               2..16; 0 = 8).  Ignored on the shared grid. */
+#define RBF_GRID_SHARED 0
+#define RBF_GRID_NESTED 1
 typedef struct {
     int M;
     double period_L;
     double window_alpha;
     int csample;
+    int grid;
+    int lagrange_K;
 } rbf_fmm_params;
 
 typedef struct rbf_tree rbf_tree;
@@ -363,7 +380,8 @@ RBF_API int rbf_precond_apply(rbf_tree *t, const double *y, double *z, void *str
  * w_D = side / 2^depth) for the given expansion parameters; K is the far
  * kernel of Eq. (35) built exactly as rbf_fmm_matvec builds it (FP64).  This
  * is the per-pair error that the scaled Lemma, Eq. (33), multiplies by
- * sum |lambda_j|.  Synchronises the device. */
+ * sum |lambda_j|.  Always the shared grid's kernel (params->grid is ignored).
+ * Synchronises the device. */
 RBF_API int rbf_kernel_error(rbf_kernel kernel, double eps, int d, const rbf_fmm_params *params,
                              double side, int depth, double *max_err_host);
 

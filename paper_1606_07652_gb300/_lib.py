@@ -17,6 +17,8 @@ FP64 = 0
 FP32 = 1
 MAX_DIM = 6
 MAX_DEPTH = 10
+GRID_SHARED = 0
+GRID_NESTED = 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "librbf.so")
@@ -26,7 +28,8 @@ _c_int, _c_i64, _c_dbl, _c_vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, c
 
 
 class FmmParams(ctypes.Structure):
-    _fields_ = [("M", _c_int), ("period_L", _c_dbl), ("window_alpha", _c_dbl), ("csample", _c_int)]
+    _fields_ = [("M", _c_int), ("period_L", _c_dbl), ("window_alpha", _c_dbl), ("csample", _c_int),
+                ("grid", _c_int), ("lagrange_K", _c_int)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -162,8 +165,9 @@ def version() -> str:
     return load().rbf_version().decode()
 
 
-def _params(M=None, period_L=None, window_alpha=None, csample=1, kernel=GAUSSIAN, side=1.0):
-    if M is None and period_L is None and window_alpha is None:
+def _params(M=None, period_L=None, window_alpha=None, csample=1, kernel=GAUSSIAN, side=1.0,
+            grid=GRID_SHARED, lagrange_K=0):
+    if M is None and period_L is None and window_alpha is None and grid == GRID_SHARED:
         return None
     p = FmmParams()
     p.M = 32 if M is None else int(M)
@@ -172,6 +176,8 @@ def _params(M=None, period_L=None, window_alpha=None, csample=1, kernel=GAUSSIAN
         window_alpha = 4.5 if kernel == IMQ else 0.0
     p.window_alpha = float(window_alpha)
     p.csample = int(csample)
+    p.grid = int(grid)
+    p.lagrange_K = int(lagrange_K)
     return p
 
 
@@ -248,12 +254,12 @@ def tree_build(X, lo=None, side=1.0, depth=-1) -> Tree:
 
 
 def fmm_matvec(tree: Tree, kernel: int, eps: float, lam, u, prec=FP64, M=None, period_L=None,
-               window_alpha=None, csample=1):
+               window_alpha=None, csample=1, grid=GRID_SHARED, lagrange_K=0):
     """rbf_fmm_matvec: lam, u are float64 CUDA tensors (N,) or (nrhs, N) (rows = columns of
     the column-major N x nrhs block)."""
     nrhs = 1 if lam.dim() == 1 else lam.shape[0]
     N = lam.shape[-1]
-    p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"])
+    p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"], grid, lagrange_K)
     _check(load().rbf_fmm_matvec(tree.handle, kernel, float(eps),
                                  ctypes.byref(p) if p is not None else None, prec,
                                  _dev(lam, "float64", "lam"), N, _dev(u, "float64", "u"), N, nrhs,
@@ -280,7 +286,8 @@ def _host_ptr(a, where):
 
 
 def fmm_matvec_host(tree: Tree, kernel: int, eps: float, lam_host, u_host=None, prec=FP64,
-                    M=None, period_L=None, window_alpha=None, csample=1):
+                    M=None, period_L=None, window_alpha=None, csample=1, grid=GRID_SHARED,
+                    lagrange_K=0):
     """rbf_fmm_matvec_host: host float64 in (numpy or torch CPU, e.g. pinned), host out;
     the host <-> device copies happen inside the call."""
     if isinstance(lam_host, np.ndarray):
@@ -288,7 +295,7 @@ def fmm_matvec_host(tree: Tree, kernel: int, eps: float, lam_host, u_host=None, 
     if u_host is None:
         u_host = np.empty(tuple(lam_host.shape), dtype=np.float64)
     nrhs = 1 if len(lam_host.shape) == 1 else lam_host.shape[0]
-    p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"])
+    p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"], grid, lagrange_K)
     _check(load().rbf_fmm_matvec_host(tree.handle, kernel, float(eps),
                                       ctypes.byref(p) if p is not None else None, prec,
                                       _host_ptr(lam_host, "lam_host"), _host_ptr(u_host, "u_host"),
@@ -324,12 +331,12 @@ def direct_sum(X, kernel: int, eps: float, lam, targets, u):
 
 def interp_solve(tree: Tree, kernel: int, eps: float, u, lam, restart_m=50, max_iters=2000,
                  max_refine=10, rtol=1e-8, inner_prec=FP32, precond=0, M=None, period_L=None,
-                 window_alpha=None, csample=1):
+                 window_alpha=None, csample=1, grid=GRID_SHARED, lagrange_K=0):
     """rbf_interp_solve: u, lam float64 CUDA tensors (N,) or (nrhs, N); lam holds the guess."""
     nrhs = 1 if u.dim() == 1 else u.shape[0]
     o = SolveOpts(restart_m, max_iters, max_refine, rtol, inner_prec, precond)
     rep = SolveReport()
-    p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"])
+    p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"], grid, lagrange_K)
     code = load().rbf_interp_solve(tree.handle, kernel, float(eps),
                                    ctypes.byref(p) if p is not None else None,
                                    _dev(u, "float64", "u"), _dev(lam, "float64", "lam"), nrhs,
@@ -472,7 +479,7 @@ def precond_apply(tree: Tree, y, z):
 
 def kernel_error(kernel, eps, d, M, period_L, window_alpha, side=1.0, depth=2) -> float:
     """rbf_kernel_error: max |K - Phi| over sampled far offsets."""
-    p = FmmParams(M, period_L, window_alpha, 1)
+    p = FmmParams(M, period_L, window_alpha, 1, GRID_SHARED, 0)
     e = _c_dbl(0)
     _check(load().rbf_kernel_error(kernel, float(eps), d, ctypes.byref(p), float(side), depth,
                                    ctypes.byref(e)), "rbf_kernel_error")

@@ -154,8 +154,11 @@ extern "C" int rbf_kernel_error(rbf_kernel kernel, double eps, int d, const rbf_
     t.d = d;
     t.D = depth;
     t.side = side;
+    // the far kernel K of the shared grid
+    rbf_fmm_params q = *p;
+    q.grid = RBF_GRID_SHARED;
     rbf_plan *pl = nullptr;
-    int st = rbf_plan_get(&t, kernel, eps, p, RBF_FP64, 0, &pl);
+    int st = rbf_plan_get(&t, kernel, eps, &q, RBF_FP64, 0, &pl);
     if (st != RBF_OK) {
         t.plan[0] = nullptr;
         return st;
@@ -196,7 +199,7 @@ extern "C" int rbf_autotune(rbf_kernel kernel, double eps, int d, int64_t N, dou
     while (d * D > 63) --D;
     // period and taper: the Gaussian needs Phi(L - side) below tol, the inverse
     // multiquadric a taper between side and L - side
-    rbf_fmm_params p;
+    rbf_fmm_params p{};
     p.csample = 1;
     if (kernel == RBF_GAUSSIAN) {
         p.window_alpha = 0.0;
@@ -295,7 +298,7 @@ extern "C" int rbf_batch_create(const rbf_problem *probs, int np, double tol_ker
             st = RBF_EINVAL;
             break;
         }
-        rbf_fmm_params prm;
+        rbf_fmm_params prm{};
         int D = 2;
         double err = 0.0;
         st = rbf_autotune(q.kernel, q.eps, q.d, q.N, 1.0, tol_kernel, &prm, &D, &err);

@@ -1080,6 +1080,7 @@ template <typename R>
 int rbf_run_far(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStream_t s)
 {
     using C = cplx<R>;
+    if (p->grid == RBF_GRID_NESTED) return rbf_run_far_nested<R>(t, p, lam_s, u_far, s);
     const int D = t->D;
     RBF_TRY(rbf_run_p2m<R>(t, p, lam_s, (C *)p->V[D], s));
     RBF_TRY(rbf_run_m2m<R>(t, p, (const C *)p->V[D], s));
@@ -1094,4 +1095,8 @@ template int rbf_run_p2m<float>(rbf_tree *, const rbf_plan *, const float *, flo
 template int rbf_run_l2p<float>(rbf_tree *, const rbf_plan *, const float2 *, float *, cudaStream_t);
 template int rbf_run_m2l<float>(rbf_tree *, const rbf_plan *, const float2 *, float2 *, cudaStream_t);
 template int rbf_run_far<double>(rbf_tree *, const rbf_plan *, const double *, double *,
+                                 cudaStream_t);
+template int rbf_run_p2m<double>(rbf_tree *, const rbf_plan *, const double *, double2 *,
+                                 cudaStream_t);
+template int rbf_run_l2p<double>(rbf_tree *, const rbf_plan *, const double2 *, double *,
                                  cudaStream_t);

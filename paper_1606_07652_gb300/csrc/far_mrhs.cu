@@ -1051,7 +1051,10 @@ int launch_l2p(const TcArgs &a, const float2 *Eg, int rowpadE, int Rg, int nptil
 
 }  // namespace
 
-int rbf_far_multi_supported(const rbf_plan *p) { return p->ncol <= kMaxNT; }
+int rbf_far_multi_supported(const rbf_plan *p)
+{
+    return p->ncol <= kMaxNT && p->grid == RBF_GRID_SHARED;
+}
 
 int rbf_run_far_multi(rbf_tree *t, rbf_plan *p, const float *lam_s, int G, float2 *V, float2 *L,
                       float *u_far, cudaStream_t s)

@@ -170,6 +170,8 @@ void rbf_default_params(rbf_kernel kernel, double side, rbf_fmm_params *p)
     p->period_L = 4.0 * side;
     p->window_alpha = kernel == RBF_IMQ ? 4.5 : 0.0;
     p->csample = 1;
+    p->grid = RBF_GRID_SHARED;
+    p->lagrange_K = 0;
 }
 
 void rbf_plan_free(rbf_plan *p)
@@ -191,16 +193,18 @@ void rbf_plan_free(rbf_plan *p)
     rbf_free(p->mr_uf);
     rbf_free(p->mr_E);
     rbf_free(p->mr_Lt);
+    rbf_nested_free(p);
     delete p;
 }
 
+// omegaC (half-spectrum weight * omega * C, nmode entries) of one grid: period L,
+// taper flat on |t| <= R_in; written to dst in the arithmetic R
 template <typename R>
-static int build_tables(rbf_tree *t, rbf_plan *p, cudaStream_t s)
+static int make_omegaC(int d, int kernel, double eps, int M, double L, double alpha, double R_in,
+                       int csample, int64_t nmode, R *dst, cudaStream_t s)
 {
-    const int d = t->d, M = p->M;
-    // coefficients
     double *Chalf = nullptr;
-    if (!p->csample) {
+    if (!csample) {
         RBF_TRY(rbf_alloc(&Chalf, 1));
     } else {
         int64_t n = 1;
@@ -208,8 +212,7 @@ static int build_tables(rbf_tree *t, rbf_plan *p, cudaStream_t s)
         double *a = nullptr, *b = nullptr;
         RBF_TRY(rbf_alloc(&a, n));
         RBF_TRY(rbf_alloc(&b, n));
-        k_lattice<<<ceil_div(n, 128), 128, 0, s>>>(p->kernel, p->eps, d, M, p->L, p->alpha,
-                                                   t->side, a, n);
+        k_lattice<<<ceil_div(n, 128), 128, 0, s>>>(kernel, eps, d, M, L, alpha, R_in, a, n);
         RBF_LAUNCH_CHECK();
         int shape[RBF_MAX_DIM];
         for (int q = 0; q < d; ++q) shape[q] = M;
@@ -229,10 +232,20 @@ static int build_tables(rbf_tree *t, rbf_plan *p, cudaStream_t s)
         rbf_free(b);
         rbf_free(shape_d);
     }
-    RBF_TRY(rbf_alloc(reinterpret_cast<R **>(&p->omegaC), p->nmode));
-    k_fill_omegaC<R><<<ceil_div(p->nmode, 256), 256, 0, s>>>(Chalf, d, M, p->L, !p->csample, p->eps,
-                                                             (R *)p->omegaC, p->nmode);
+    k_fill_omegaC<R><<<ceil_div(nmode, 256), 256, 0, s>>>(Chalf, d, M, L, !csample, eps, dst, nmode);
     RBF_LAUNCH_CHECK();
+    RBF_CUDA_TRY(cudaStreamSynchronize(s));
+    rbf_free(Chalf);
+    return RBF_OK;
+}
+
+template <typename R>
+static int build_tables(rbf_tree *t, rbf_plan *p, cudaStream_t s)
+{
+    const int d = t->d, M = p->M;
+    RBF_TRY(rbf_alloc(reinterpret_cast<R **>(&p->omegaC), p->nmode));
+    RBF_TRY(make_omegaC<R>(d, p->kernel, p->eps, M, p->L, p->alpha, t->side, p->csample, p->nmode,
+                           (R *)p->omegaC, s));
     RBF_TRY(rbf_alloc(reinterpret_cast<R **>(&p->xi), M + 1));
     k_fill_xi<R><<<1, 128, 0, s>>>((R *)p->xi, M, p->L);
     RBF_LAUNCH_CHECK();
@@ -247,8 +260,15 @@ static int build_tables(rbf_tree *t, rbf_plan *p, cudaStream_t s)
     k_fill_shift_ph<R><<<ceil_div(nsh, 256), 256, 0, s>>>((cplx<R> *)p->shift_ph, t->D, M, p->L, t->side);
     RBF_LAUNCH_CHECK();
     RBF_CUDA_TRY(cudaStreamSynchronize(s));
-    rbf_free(Chalf);
     return RBF_OK;
+}
+
+int rbf_make_omegaC(int prec, int d, int kernel, double eps, int M, double L, double alpha,
+                    double R_in, int csample, int64_t nmode, void *dst, cudaStream_t s)
+{
+    if (prec == RBF_FP64)
+        return make_omegaC<double>(d, kernel, eps, M, L, alpha, R_in, csample, nmode, (double *)dst, s);
+    return make_omegaC<float>(d, kernel, eps, M, L, alpha, R_in, csample, nmode, (float *)dst, s);
 }
 
 template <typename R>
@@ -284,12 +304,26 @@ int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_param
     RBF_REQUIRE(pp->csample == 1 || kernel == RBF_GAUSSIAN,
                 "closed-form coefficients exist for the Gaussian only");
     RBF_REQUIRE(prec == RBF_FP64 || prec == RBF_FP32, "unknown precision %d", prec);
+    RBF_REQUIRE(pp->grid == RBF_GRID_SHARED || pp->grid == RBF_GRID_NESTED, "unknown grid %d", pp->grid);
+    const int lagK = pp->grid == RBF_GRID_NESTED ? (pp->lagrange_K ? pp->lagrange_K : 8) : 0;
+    if (pp->grid == RBF_GRID_NESTED) {
+        if (t->d > 3) {
+            rbf_set_error("nested grids are built for d <= 3 (d = %d)", t->d);
+            return RBF_ENOTSUP;
+        }
+        RBF_REQUIRE(lagK >= 2 && lagK <= 16 && lagK % 2 == 0, "lagrange_K=%d must be even in [2, 16]",
+                    lagK);
+        RBF_REQUIRE(pp->M >= 2 * lagK, "nested grids need M >= 2 lagrange_K (M=%d, K=%d)", pp->M, lagK);
+        RBF_REQUIRE(pp->csample == 1 && pp->window_alpha > 0.0,
+                    "nested grids need sampled coefficients and a taper (window_alpha > 0)");
+    }
     rbf_plan *p = t->plan[prec];
     const int d = t->d, M = pp->M;
     int64_t nmode = M / 2 + 1;
     for (int q = 1; q < d; ++q) nmode *= (M + 1);
     if (p && p->kernel == kernel && p->eps == eps && p->M == M && p->L == pp->period_L &&
-        p->alpha == pp->window_alpha && p->csample == pp->csample) {
+        p->alpha == pp->window_alpha && p->csample == pp->csample && p->grid == pp->grid &&
+        p->lagK == lagK) {
         *out = p;
         return RBF_OK;
     }
@@ -305,6 +339,7 @@ int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_param
         rbf_free(p->root_ph);
         rbf_free(p->shift_ph);
         p->omegaC = p->xi = p->root_ph = p->shift_ph = nullptr;
+        rbf_nested_free(p);
     }
     p->prec = prec;
     p->kernel = kernel;
@@ -313,6 +348,8 @@ int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_param
     p->L = pp->period_L;
     p->alpha = pp->window_alpha;
     p->csample = pp->csample;
+    p->grid = pp->grid;
+    p->lagK = lagK;
     p->n0 = M / 2 + 1;
     p->n1 = M + 1;
     p->nmode = nmode;
@@ -326,6 +363,7 @@ int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_param
     }
     int st = prec == RBF_FP64 ? build_tables<double>(t, p, s) : build_tables<float>(t, p, s);
     if (st == RBF_OK && fresh) st = prec == RBF_FP64 ? alloc_work<double>(t, p) : alloc_work<float>(t, p);
+    if (st == RBF_OK && p->grid == RBF_GRID_NESTED) st = rbf_nested_build(t, p, s);
     if (st != RBF_OK) {
         rbf_plan_free(p);
         t->plan[prec] = nullptr;

@@ -207,11 +207,33 @@ struct rbf_plan {
     float *mr_uf = nullptr;    // [mr_G][N]
     float2 *mr_E = nullptr;    // [N][even_up(n0 + (d-1) n1)] point phase tables of P2M
     float *mr_Lt = nullptr;    // [N][16] coefficients of a group, point-major
+    // nested (scale-invariant) grids of Sec. 4.1.1 (grid == RBF_GRID_NESTED), nested.cu
+    int grid = RBF_GRID_SHARED;
+    int lagK = 0, lagKT = 0;   // taps of the interpolation and of its transpose
+    void *nest_wc[RBF_MAX_DEPTH + 1] = {nullptr};  // [nmode] omega_l C_l, levels 2..D
+    void *nest_xi = nullptr;   // [n1] nodes of the leaf grid
+    void *nest_ph = nullptr;   // [15][n1] complex translation phases (level independent)
+    int32_t *lag_fidx = nullptr;  // [n1][lagK] child node of each tap (k + M/2)
+    void *lag_fw = nullptr;       // [n1][lagK] interpolation weights
+    int32_t *lag_tidx = nullptr;  // [n1][lagKT] parent node of each transposed tap
+    void *lag_tw = nullptr;       // [n1][lagKT] transposed weights (0 in padding)
+    int32_t *nest_nbr[RBF_MAX_DEPTH + 1] = {nullptr};  // [nbox_l][3^d] neighbours, levels 1..D
+    void *nest_Vt[RBF_MAX_DEPTH + 1] = {nullptr};  // parents on their children's grid, 1..D-1
+    void *nest_L[RBF_MAX_DEPTH + 1] = {nullptr};   // local expansions, levels 2..D-1 (D: Lleaf)
+    void *nest_tmp[2] = {nullptr, nullptr};        // [nleaf][mstride] pass buffers
 };
 
 int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_params *p, int prec,
                  cudaStream_t s, rbf_plan **out);
 void rbf_plan_free(rbf_plan *p);
+// omegaC of one grid (period L, taper flat on |t| <= R_in) into dst ([nmode], FP64 or FP32)
+int rbf_make_omegaC(int prec, int d, int kernel, double eps, int M, double L, double alpha,
+                    double R_in, int csample, int64_t nmode, void *dst, cudaStream_t s);
+// nested grids (nested.cu): tables and per-level workspace; free; the far field
+int rbf_nested_build(rbf_tree *t, rbf_plan *p, cudaStream_t s);
+void rbf_nested_free(rbf_plan *p);
+template <typename R>
+int rbf_run_far_nested(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStream_t s);
 
 // Far-field and near-field passes (expansions.cu, p2p.cu)
 template <typename R>
