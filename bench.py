@@ -270,6 +270,8 @@ def run_ours(args):
                "passes": passes}
         if not args.skip_extra:
             out.update(extra_measurements(rbf, tree, Xd, ld, targets, p, kw, dev))
+        if args.nested:
+            out["nested_grid"] = nested_measurement(rbf, tree, Xd, ld, targets, p, kw, dev)
         if args.batch:
             out["batch"] = batch_measurement(rbf, dev)
         if args.solve:
@@ -315,6 +317,67 @@ def extra_measurements(rbf, tree, Xd, ld, targets, p, kw, dev):
 
     return {"fp64": {"value": N / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64},
             "error_vs_direct_4096_targets": {"fp32": err(u32), "fp64": err(u64)}}
+
+
+def nested_measurement(rbf, tree, Xd, ld, targets, p, kw, dev, steps=5, K=8):
+    """The same workload on the nested (scale-invariant) grids of Sec. 4.1.1: FP32
+    products timed with CUDA events, per-pass device times, and the error of the
+    FP32 and FP64 nested products against the FP64 direct sum on the same targets."""
+    import torch
+    info = tree.info()
+    N = ld.shape[0]
+    kwn = dict(kw, grid=rbf.GRID_NESTED, lagrange_K=K)
+    u = torch.empty_like(ld)
+    for _ in range(2):
+        rbf.fmm_matvec(tree, p["kernel"], p["eps"], ld, u, prec=rbf.FP32, **kwn)
+    torch.cuda.synchronize()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    rbf.profile(tree, True)
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rbf.fmm_matvec(tree, p["kernel"], p["eps"], ld, u, prec=rbf.FP32, **kwn)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    prof = rbf.profile_read(tree)
+    rbf.profile(tree, False)
+    u64 = torch.empty_like(ld)
+    rbf.fmm_matvec(tree, p["kernel"], p["eps"], ld, u64, prec=rbf.FP64, **kwn)
+    tg = torch.as_tensor(np.asarray(targets, dtype=np.int64), device=dev)
+    ud = torch.empty(len(targets), dtype=torch.float64, device=dev)
+    rbf.direct_sum(Xd, p["kernel"], p["eps"], ld, tg, ud)
+    torch.cuda.synchronize()
+    ud_h = ud.cpu().numpy()
+
+    def err(v):
+        v = v.cpu().numpy()[targets]
+        return float(np.linalg.norm(v - ud_h) / np.linalg.norm(ud_h))
+
+    # algorithmic HBM bytes of the translation passes (FP32 complex = 8 B per mode)
+    nmode = (p["M"] // 2 + 1) * (p["M"] + 1) ** 2
+    nb = info["n_box"]
+    D = info["depth"]
+    up = sum((nb[l] + 2 * nb[l - 1]) * nmode * 8.0 for l in range(2, D + 1))
+    cpl = sum((2 * nb[l] + nb[l - 1]) * nmode * 8.0 for l in range(2, D + 1))
+    cpl += sum((nb[l - 1] + 2 * nb[l]) * nmode * 8.0 for l in range(3, D + 1))
+    hbm = _peaks()["hbm_gbs"]
+    passes = {}
+    for name, v in prof.items():
+        if v["launches"]:
+            passes[name] = {"ms_per_step": v["ms"] / steps, "launches": v["launches"] // steps}
+    for name, b in (("m2m", up), ("m2l", cpl)):
+        if name in passes:
+            gbs = b / 1e9 / (passes[name]["ms_per_step"] / 1e3)
+            passes[name].update({"algorithmic_GB": b / 1e9, "achieved_GBs": gbs,
+                                 "frac_of_hbm": gbs / hbm})
+    t = float(np.mean(ms))
+    return {"workload": "same tree and M; nested grids, Lagrange stencil K=%d" % K,
+            "ms_per_step": t, "points_per_s": N / (t / 1e3),
+            "rel_err_vs_direct": {"fp32": err(u), "fp64": err(u64)},
+            "passes": passes}
 
 
 def batch_measurement(rbf, dev, n_problems=256, steps=5):
@@ -542,6 +605,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=60.0)
     ap.add_argument("--n", type=int, default=0, help="override the number of centres (profiling)")
     ap.add_argument("--batch", type=int, default=1, help="also time the 256-problem batch")
+    ap.add_argument("--nested", type=int, default=1, help="also time the nested-grid product")
     ap.add_argument("--solve", type=int, default=1, help="also run the solve comparison")
     ap.add_argument("--mrhs", type=int, default=1,
                     help="also time the 5D 16-column product on the tensor cores")
