@@ -272,6 +272,8 @@ def run_ours(args):
             out.update(extra_measurements(rbf, tree, Xd, ld, targets, p, kw, dev))
         if args.nested:
             out["nested_grid"] = nested_measurement(rbf, tree, Xd, ld, targets, p, kw, dev)
+        if args.kernels:
+            out["three_kernels"] = kernels_measurement(rbf, dev)
         if args.batch:
             out["batch"] = batch_measurement(rbf, dev)
         if args.solve:
@@ -378,6 +380,47 @@ def nested_measurement(rbf, tree, Xd, ld, targets, p, kw, dev, steps=5, K=8):
             "ms_per_step": t, "points_per_s": N / (t / 1e3),
             "rel_err_vs_direct": {"fp32": err(u), "fp64": err(u64)},
             "passes": passes}
+
+
+def kernels_measurement(rbf, dev, n=1 << 20, depths=(4, 5), Ms=(16, 24, 32)):
+    """The three kernels of the paper's numerical examples (Sec. 5): IMQ and MQ with
+    eps = 1, Wendland (1 - eps r)_+^3 (3 eps r + 1) with eps = 0.5, on 3-D uniform
+    centres in the unit cube: for each tree depth and M, the FP32 product time and its
+    max-norm error on 1024 targets relative to max |u| of the FP64 direct sum."""
+    import torch
+    import workloads
+    X, lam = workloads.uniform(n, 3, 77)
+    Xd = torch.as_tensor(X, device=dev)
+    ld = torch.as_tensor(lam, device=dev)
+    tg_h = np.random.default_rng(78).choice(n, 1024, replace=False)
+    tg = torch.as_tensor(tg_h.astype(np.int64), device=dev)
+    kernels = (("IMQ", rbf.IMQ, 1.0, 4.5), ("MQ", rbf.MQ, 1.0, 4.5),
+               ("Wendland", rbf.WENDLAND, 0.5, 0.0))
+    out = {}
+    u = torch.empty_like(ld)
+    for name, k, eps, alpha in kernels:
+        ud = torch.empty(1024, dtype=torch.float64, device=dev)
+        rbf.direct_sum(Xd, k, eps, ld, tg, ud)
+        torch.cuda.synchronize()
+        umax = float(ud.abs().max())
+        rows = []
+        for D in depths:
+            t = rbf.tree_build(Xd, lo=np.zeros(3), side=1.0, depth=D)
+            for M in Ms:
+                kw = dict(prec=rbf.FP32, M=M, period_L=4.0, window_alpha=alpha)
+                rbf.fmm_matvec(t, k, eps, ld, u, **kw)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                rbf.fmm_matvec(t, k, eps, ld, u, **kw)
+                e1.record()
+                torch.cuda.synchronize()
+                err = float((u[tg] - ud).abs().max()) / umax
+                rows.append({"depth": D, "M": M, "ms": e0.elapsed_time(e1), "linf_rel": err})
+            t.free()
+        out[name] = {"eps": eps, "window_alpha": alpha, "results": rows}
+    return {"workload": "3D N=%d uniform in [0,1]^3, L=4, FP32 products, 1024 targets" % n,
+            "kernels": out}
 
 
 def batch_measurement(rbf, dev, n_problems=256, steps=5):
@@ -606,6 +649,8 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override the number of centres (profiling)")
     ap.add_argument("--batch", type=int, default=1, help="also time the 256-problem batch")
     ap.add_argument("--nested", type=int, default=1, help="also time the nested-grid product")
+    ap.add_argument("--kernels", type=int, default=1,
+                    help="also run the IMQ / MQ / Wendland error-vs-M sweep")
     ap.add_argument("--solve", type=int, default=1, help="also run the solve comparison")
     ap.add_argument("--mrhs", type=int, default=1,
                     help="also time the 5D 16-column product on the tensor cores")

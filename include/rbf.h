@@ -51,10 +51,14 @@ extern "C" {
 #define RBF_MAX_DIM 6
 #define RBF_MAX_DEPTH 10
 
-/* Radial kernels of the table "Global functions" (Sec. 2.2) in shape-parameter
- * form: Gaussian Phi(r) = exp(-(eps r)^2); inverse multiquadric
- * Phi(r) = 1/sqrt(1 + (eps r)^2).  Both have Phi(0) = 1. */
-typedef enum { RBF_GAUSSIAN = 0, RBF_IMQ = 1 } rbf_kernel;
+/* Radial kernels of the tables "Global functions" and "Compactly supported
+ * functions" (Sec. 2.2) in shape-parameter form: Gaussian
+ * Phi(r) = exp(-(eps r)^2); inverse multiquadric Phi(r) = 1/sqrt(1 + (eps r)^2);
+ * multiquadric Phi(r) = sqrt(1 + (eps r)^2); Wendland
+ * Phi(r) = (1 - eps r)_+^3 (3 eps r + 1) (Phi_{2,1}, support radius 1/eps; the
+ * compact kernel of the numerical examples, Sec. 5).  All have Phi(0) = 1.
+ * The multiquadric grows with r and needs the taper (window_alpha > 0). */
+typedef enum { RBF_GAUSSIAN = 0, RBF_IMQ = 1, RBF_MQ = 2, RBF_WENDLAND = 3 } rbf_kernel;
 
 /* Arithmetic of the matrix-vector product.  Inputs and outputs of
  * rbf_fmm_matvec are FP64 in both cases. */

@@ -55,6 +55,8 @@ import numpy as np
 
 GAUSSIAN = 0
 IMQ = 1
+MQ = 2
+WENDLAND = 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
@@ -98,13 +100,20 @@ _D = ctypes.c_double
 
 
 # --------------------------------------------------------------------------
-# Kernels: Table "Global functions" (Sec. 2.2), shape-parameter form.
+# Kernels: Tables "Global functions" and "Compactly supported functions"
+# (Sec. 2.2), shape-parameter form.
 # --------------------------------------------------------------------------
 def phi(kernel: int, eps: float, r):
-    """Phi(r) = exp(-(eps r)^2) (Gaussian) or 1/sqrt(1+(eps r)^2) (IMQ)."""
+    """Phi(r) = exp(-(eps r)^2) (Gaussian), 1/sqrt(1+(eps r)^2) (IMQ),
+    sqrt(1+(eps r)^2) (MQ) or (1 - eps r)_+^3 (3 eps r + 1) (Wendland Phi_{2,1})."""
     er = eps * np.asarray(r, dtype=np.float64)
     if kernel == GAUSSIAN:
         return np.exp(-er * er)
+    if kernel == MQ:
+        return np.sqrt(1.0 + er * er)
+    if kernel == WENDLAND:
+        t = np.where(er < 1.0, 1.0 - er, 0.0)
+        return t * t * t * (3.0 * er + 1.0)
     return 1.0 / np.sqrt(1.0 + er * er)
 
 

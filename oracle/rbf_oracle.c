@@ -33,14 +33,21 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_GAUSSIAN = 0, ORC_IMQ = 1 };
+enum { ORC_GAUSSIAN = 0, ORC_IMQ = 1, ORC_MQ = 2, ORC_WENDLAND = 3 };
 
-/* Table "Global functions" (Sec. 2.2) in the shape-parameter form
- * Phi(r) = exp(-(eps r)^2)  and  Phi(r) = 1/sqrt(1+(eps r)^2). */
+/* Tables "Global functions" and "Compactly supported functions" (Sec. 2.2) in
+ * the shape-parameter form: Phi(r) = exp(-(eps r)^2), 1/sqrt(1+(eps r)^2),
+ * sqrt(1+(eps r)^2), and the compact Phi_{2,1}(eps r) = (1 - eps r)_+^3 (3 eps r + 1)
+ * (the Wendland function of Sec. 5). */
 double orc_phi(int kernel, double eps, double r)
 {
     double er = eps * r;
     if (kernel == ORC_GAUSSIAN) return exp(-er * er);
+    if (kernel == ORC_MQ) return sqrt(1.0 + er * er);
+    if (kernel == ORC_WENDLAND) {
+        double t = er < 1.0 ? 1.0 - er : 0.0;
+        return t * t * t * (3.0 * er + 1.0);
+    }
     return 1.0 / sqrt(1.0 + er * er);
 }
 

@@ -13,6 +13,8 @@ import numpy as np
 
 GAUSSIAN = 0
 IMQ = 1
+MQ = 2
+WENDLAND = 3
 FP64 = 0
 FP32 = 1
 MAX_DIM = 6
@@ -173,7 +175,7 @@ def _params(M=None, period_L=None, window_alpha=None, csample=1, kernel=GAUSSIAN
     p.M = 32 if M is None else int(M)
     p.period_L = 4.0 * side if period_L is None else float(period_L)
     if window_alpha is None:
-        window_alpha = 4.5 if kernel == IMQ else 0.0
+        window_alpha = 0.0 if kernel == GAUSSIAN else 4.5
     p.window_alpha = float(window_alpha)
     p.csample = int(csample)
     p.grid = int(grid)

@@ -61,8 +61,7 @@ __global__ void k_kernel_error(int d, int M, int64_t nmode, const double *xi, co
         ph += xi[rr + M / 2] * r[0];
         K += omegaC[m] * cos(ph);
     }
-    const double e2 = eps * eps * r2;
-    const double phi = kernel == RBF_GAUSSIAN ? exp(-e2) : 1.0 / sqrt(1.0 + e2);
+    const double phi = rbf_phi64(kernel, eps * eps * r2);
     err[q] = fabs(K - phi);
 }
 
@@ -197,14 +196,18 @@ extern "C" int rbf_autotune(rbf_kernel kernel, double eps, int d, int64_t N, dou
     int D = (int)std::lround(std::log(std::max(1.0, (double)N / per_leaf)) / std::log((double)(1 << d)));
     D = std::max(2, std::min(D, RBF_MAX_DEPTH));
     while (d * D > 63) --D;
-    // period and taper: the Gaussian needs Phi(L - side) below tol, the inverse
-    // multiquadric a taper between side and L - side
+    // period and taper: the Gaussian needs Phi(L - side) below tol; the Wendland
+    // function needs its support 1/eps inside L - side; the (inverse) multiquadric a
+    // taper between side and L - side
     rbf_fmm_params p{};
     p.csample = 1;
     if (kernel == RBF_GAUSSIAN) {
         p.window_alpha = 0.0;
         p.period_L = side + std::sqrt(std::max(0.0, -std::log(0.01 * tol))) / eps;
         p.period_L = std::max(p.period_L, 1.25 * side);
+    } else if (kernel == RBF_WENDLAND) {
+        p.window_alpha = 0.0;
+        p.period_L = std::max(side + 1.0 / eps, 1.25 * side) * 1.0000001;
     } else {
         p.window_alpha = 4.5;
         p.period_L = 4.0 * side;
@@ -219,8 +222,10 @@ extern "C" int rbf_autotune(rbf_kernel kernel, double eps, int d, int64_t N, dou
         return rbf_kernel_error(kernel, eps, d, &p, side, D, e);
     };
     const double lt = std::log(1.0 / tol);
+    // (the Wendland function's transform decays only algebraically: start at 16)
     const double pred = kernel == RBF_GAUSSIAN ? 2.0 * eps * p.period_L * std::sqrt(lt) / M_PI
-                                               : eps * p.period_L * lt / M_PI;
+                        : kernel == RBF_WENDLAND ? 16.0
+                                                 : eps * p.period_L * lt / M_PI;
     int M0 = 2 * (int)std::lround(pred / 2.0);
     M0 = std::max(8, std::min(64, M0));
     double err = INFINITY;

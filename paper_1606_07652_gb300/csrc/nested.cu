@@ -116,11 +116,12 @@ __global__ void __launch_bounds__(kThreads) k_vt(int M, int n1, int64_t nmode, i
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_axis(int n1, int64_t nmode, int64_t ms, int64_t stride,
                                                    int ntap, const int32_t *idx, const R *w,
-                                                   const cplx<R> *in, cplx<R> *out, int accumulate)
+                                                   const cplx<R> *in, cplx<R> *out, int accumulate,
+                                                   int nch)
 {
     using C = cplx<R>;
-    const int64_t b = blockIdx.x;
-    const int64_t m = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    const int64_t b = blockIdx.x / nch;  // mode chunks of one box run back to back
+    const int64_t m = (int64_t)(blockIdx.x % nch) * blockDim.x + threadIdx.x;
     if (m >= nmode) return;
     const int dig = (int)((m / stride) % n1);
     const C *src = in + b * ms + (m - (int64_t)dig * stride);
@@ -148,11 +149,11 @@ __global__ void __launch_bounds__(kThreads) k_m2m_last(int M, int n1, int64_t nm
                                                        const R *fw, const cplx<R> *ph,
                                                        const int32_t *child_off,
                                                        const uint64_t *child_key, const cplx<R> *T,
-                                                       cplx<R> *Vp)
+                                                       cplx<R> *Vp, int nch)
 {
     using C = cplx<R>;
-    const int p = blockIdx.x;
-    const int64_t m = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    const int p = (int)(blockIdx.x / nch);  // the taps of one parent's rows stay in L2
+    const int64_t m = (int64_t)(blockIdx.x % nch) * blockDim.x + threadIdx.x;
     if (m >= nmode) return;
     int kk[DIM];
     mode_digits<DIM>(m, n1, M, kk);
@@ -189,11 +190,11 @@ __global__ void __launch_bounds__(kThreads) k_l2l_first(int M, int n1, int64_t n
                                                         const R *tw, const cplx<R> *ph,
                                                         const int32_t *parent, const uint64_t *key,
                                                         const cplx<R> *Lp, cplx<R> *out,
-                                                        int accumulate)
+                                                        int accumulate, int nch)
 {
     using C = cplx<R>;
-    const int64_t c = blockIdx.x;
-    const int64_t m = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    const int64_t c = blockIdx.x / nch;
+    const int64_t m = (int64_t)(blockIdx.x % nch) * blockDim.x + threadIdx.x;
     if (m >= nmode) return;
     int kk[DIM];
     mode_digits<DIM>(m, n1, M, kk);
@@ -481,15 +482,15 @@ int run_nested(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStr
             const C *src = (const C *)p->V[l];
             int pb = 0;
             for (int ax = d - 1; ax >= 1; --ax) {
-                k_axis<R><<<dim3(lc.nbox, ych), kThreads, 0, s>>>(n1, nmode, ms, stride_of(ax), K,
-                                                                  p->lag_fidx, fw, src, tmp[pb], 0);
+                k_axis<R><<<(unsigned)lc.nbox * ych, kThreads, 0, s>>>(
+                    n1, nmode, ms, stride_of(ax), K, p->lag_fidx, fw, src, tmp[pb], 0, (int)ych);
                 RBF_LAUNCH_CHECK();
                 src = tmp[pb];
                 pb ^= 1;
             }
-            k_m2m_last<R, DIM><<<dim3(lp.nbox, ych), kThreads, 0, s>>>(
+            k_m2m_last<R, DIM><<<(unsigned)lp.nbox * ych, kThreads, 0, s>>>(
                 M, n1, nmode, ms, rows, K, p->lag_fidx, fw, ph, lp.child_off, lc.key, src,
-                (C *)p->V[l - 1]);
+                (C *)p->V[l - 1], (int)ych);
             RBF_LAUNCH_CHECK();
         }
     }
@@ -508,21 +509,23 @@ int run_nested(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStr
             C *Ll = l == D ? (C *)p->Lleaf : (C *)p->nest_L[l];
             const C *Lp = (const C *)p->nest_L[l - 1];
             if (d == 1) {
-                k_l2l_first<R, DIM><<<dim3(lv.nbox, ych), kThreads, 0, s>>>(
-                    M, n1, nmode, ms, rows, KT, p->lag_tidx, tw, ph, lv.parent, lv.key, Lp, Ll, 1);
+                k_l2l_first<R, DIM><<<(unsigned)lv.nbox * ych, kThreads, 0, s>>>(
+                    M, n1, nmode, ms, rows, KT, p->lag_tidx, tw, ph, lv.parent, lv.key, Lp, Ll, 1,
+                    (int)ych);
                 RBF_LAUNCH_CHECK();
                 continue;
             }
-            k_l2l_first<R, DIM><<<dim3(lv.nbox, ych), kThreads, 0, s>>>(
-                M, n1, nmode, ms, rows, KT, p->lag_tidx, tw, ph, lv.parent, lv.key, Lp, tmp[0], 0);
+            k_l2l_first<R, DIM><<<(unsigned)lv.nbox * ych, kThreads, 0, s>>>(
+                M, n1, nmode, ms, rows, KT, p->lag_tidx, tw, ph, lv.parent, lv.key, Lp, tmp[0], 0,
+                (int)ych);
             RBF_LAUNCH_CHECK();
             const C *src = tmp[0];
             int pb = 1;
             for (int ax = 1; ax < d; ++ax) {
                 const bool last = ax == d - 1;
                 C *dst = last ? Ll : tmp[pb];
-                k_axis<R><<<dim3(lv.nbox, ych), kThreads, 0, s>>>(n1, nmode, ms, stride_of(ax), KT,
-                                                                  p->lag_tidx, tw, src, dst, last);
+                k_axis<R><<<(unsigned)lv.nbox * ych, kThreads, 0, s>>>(
+                    n1, nmode, ms, stride_of(ax), KT, p->lag_tidx, tw, src, dst, last, (int)ych);
                 RBF_LAUNCH_CHECK();
                 src = dst;
                 pb ^= 1;

@@ -7,6 +7,7 @@
 // quarter of the staged sources, lane = target, so every shared-memory read is
 // a broadcast.  The four partial sums of a target are added in a fixed order.
 #include <algorithm>
+#include <type_traits>
 
 #include "rbf_internal.cuh"
 
@@ -36,19 +37,47 @@ struct Src4<double> {
     using type = double4_32a;
 };
 
-// Phi in the product's arithmetic: exp(-(eps r)^2) or 1/sqrt(1 + (eps r)^2).
-__device__ __forceinline__ float phi_r2(int kernel, float e2, float r2)
+// Phi in the product's arithmetic, the kernel fixed at compile time:
+// exp(-(eps r)^2), 1/sqrt(1 + (eps r)^2), sqrt(1 + (eps r)^2) or
+// (1 - eps r)_+^3 (3 eps r + 1).
+template <int KER>
+__device__ __forceinline__ float phi_r2(float e2, float r2)
 {
-    // Gaussian through exp2: e2 already holds eps^2 * log2(e)
-    return kernel == RBF_GAUSSIAN ? exp2f(-e2 * r2) : rsqrtf(fmaf(e2, r2, 1.0f));
+    if (KER == RBF_GAUSSIAN) return exp2f(-e2 * r2);  // e2 holds eps^2 * log2(e)
+    if (KER == RBF_IMQ) return rsqrtf(fmaf(e2, r2, 1.0f));
+    if (KER == RBF_MQ) return sqrtf(fmaf(e2, r2, 1.0f));
+    const float q = sqrtf(e2 * r2);
+    const float t = fmaxf(1.0f - q, 0.0f);
+    return t * t * t * fmaf(3.0f, q, 1.0f);
 }
-__device__ __forceinline__ double phi_r2(int kernel, double e2, double r2)
+template <int KER>
+__device__ __forceinline__ double phi_r2(double e2, double r2)
 {
-    return kernel == RBF_GAUSSIAN ? exp(-e2 * r2) : rsqrt(fma(e2, r2, 1.0));
+    if (KER == RBF_GAUSSIAN) return exp(-e2 * r2);
+    if (KER == RBF_IMQ) return rsqrt(fma(e2, r2, 1.0));
+    if (KER == RBF_MQ) return sqrt(fma(e2, r2, 1.0));
+    const double q = sqrt(e2 * r2);
+    const double t = fmax(1.0 - q, 0.0);
+    return t * t * t * fma(3.0, q, 1.0);
 }
 
-template <typename R, int DIM, int TG>
-__global__ void __launch_bounds__(P2P_THREADS) k_p2p(int kernel, R e2, int64_t N, const R *xs,
+// f(std::integral_constant<int, K>) for the run-time kernel id K
+template <typename F>
+int with_kernel(int kernel, F f)
+{
+    switch (kernel) {
+    case RBF_GAUSSIAN: return f(std::integral_constant<int, RBF_GAUSSIAN>());
+    case RBF_IMQ: return f(std::integral_constant<int, RBF_IMQ>());
+    case RBF_MQ: return f(std::integral_constant<int, RBF_MQ>());
+    case RBF_WENDLAND: return f(std::integral_constant<int, RBF_WENDLAND>());
+    default:
+        rbf_set_error("p2p: unknown kernel %d", kernel);
+        return RBF_EINVAL;
+    }
+}
+
+template <typename R, int DIM, int TG, int KER>
+__global__ void __launch_bounds__(P2P_THREADS) k_p2p(R e2, int64_t N, const R *xs,
                                                      const R *lam, const int32_t *leaf_off,
                                                      const int32_t *near_off,
                                                      const int32_t *near_idx, R *u)
@@ -170,7 +199,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int kernel, R e2, int64_t N
                             R d5 = xt[g][DIM > 5 ? 5 : 0] - r1.z;
                             r2 = fma(d5, d5, r2);
                         }
-                        acc[g][k] = fma(wgt, phi_r2(kernel, e2, r2), acc[g][k]);
+                        acc[g][k] = fma(wgt, phi_r2<KER>(e2, r2), acc[g][k]);
                     }
                 }
             }
@@ -194,16 +223,15 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(int kernel, R e2, int64_t N
     }
 }
 
-template <typename R, int TG>
-int launch_p2p_tg(int d, int kernel, R e2, const rbf_tree *t, const R *xs, const R *lam, R *u,
-                  cudaStream_t s)
+template <typename R, int TG, int KER>
+int launch_p2p_tg(int d, R e2, const rbf_tree *t, const R *xs, const R *lam, R *u, cudaStream_t s)
 {
     const int nleaf = t->nleaf();
     switch (d) {
 #define RBF_P2P_CASE(DD)                                                                          \
     case DD:                                                                                      \
-        k_p2p<R, DD, TG><<<nleaf, P2P_THREADS, 0, s>>>(kernel, e2, t->N, xs, lam, t->leaf_off,     \
-                                                       t->near_off, t->near_idx, u);               \
+        k_p2p<R, DD, TG, KER><<<nleaf, P2P_THREADS, 0, s>>>(e2, t->N, xs, lam, t->leaf_off,        \
+                                                            t->near_off, t->near_idx, u);          \
         break;
         RBF_P2P_CASE(1)
         RBF_P2P_CASE(2)
@@ -227,9 +255,11 @@ int launch_p2p(int d, int kernel, R e2, const rbf_tree *t, const R *xs, const R 
                cudaStream_t s)
 {
     const int ml = std::max<int>(1, t->max_leaf);
-    if (ml <= RBF_P2P_SMALL || RBF_P2P_TGMAX == 1)
-        return launch_p2p_tg<R, 1>(d, kernel, e2, t, xs, lam, u, s);
-    return launch_p2p_tg<R, 4>(d, kernel, e2, t, xs, lam, u, s);
+    const bool small = ml <= RBF_P2P_SMALL || RBF_P2P_TGMAX == 1;
+    return with_kernel(kernel, [&](auto K) {
+        return small ? launch_p2p_tg<R, 1, decltype(K)::value>(d, e2, t, xs, lam, u, s)
+                     : launch_p2p_tg<R, 4, decltype(K)::value>(d, e2, t, xs, lam, u, s);
+    });
 }
 
 // ---------------------------------------------- several right-hand sides --
@@ -251,8 +281,8 @@ struct P2pmShape {
     static constexpr int BUF = STAGE > RED ? STAGE : RED;
 };
 
-template <int DIM, int RG>
-__global__ void __launch_bounds__(P2P_THREADS) k_p2p_multi(int kernel, float e2, int64_t N,
+template <int DIM, int RG, int KER>
+__global__ void __launch_bounds__(P2P_THREADS) k_p2p_multi(float e2, int64_t N,
                                                            const float *xs, const float *lam,
                                                            int G, const int32_t *leaf_off,
                                                            const int32_t *near_off,
@@ -337,7 +367,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_multi(int kernel, float e2,
                             const float df = xt[g][t] - xs_[t];
                             r2 = fmaf(df, df, r2);
                         }
-                        const float ph = phi_r2(kernel, e2, r2);
+                        const float ph = phi_r2<KER>(e2, r2);
 #pragma unroll
                         for (int r = 0; r < RG; ++r) acc[g][r] = fmaf(l[r], ph, acc[g][r]);
                     }
@@ -362,17 +392,17 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_multi(int kernel, float e2,
     }
 }
 
-template <int RG>
-int launch_p2p_multi(int d, int kernel, float e2, const rbf_tree *t, const float *lam, int G,
-                     float *u, cudaStream_t s)
+template <int RG, int KER>
+int launch_p2p_multi(int d, float e2, const rbf_tree *t, const float *lam, int G, float *u,
+                     cudaStream_t s)
 {
     const int nleaf = t->nleaf();
     switch (d) {
 #define RBF_P2PM_CASE(DD)                                                                         \
     case DD:                                                                                      \
-        k_p2p_multi<DD, RG><<<nleaf, P2P_THREADS, 0, s>>>(kernel, e2, t->N, t->xs32, lam, G,      \
-                                                          t->leaf_off, t->near_off, t->near_idx,  \
-                                                          u);                                     \
+        k_p2p_multi<DD, RG, KER><<<nleaf, P2P_THREADS, 0, s>>>(e2, t->N, t->xs32, lam, G,         \
+                                                               t->leaf_off, t->near_off,          \
+                                                               t->near_idx, u);                   \
         break;
         RBF_P2PM_CASE(1)
         RBF_P2PM_CASE(2)
@@ -419,7 +449,14 @@ __global__ void __launch_bounds__(DS_THREADS) k_direct(const double *X, int64_t 
                 double df = xt[t] - sx[j * d + t];
                 r2 += df * df;
             }
-            acc += sl[j] * (kernel == RBF_GAUSSIAN ? exp(-e2 * r2) : 1.0 / sqrt(1.0 + e2 * r2));
+            double ph;
+            if (kernel == RBF_GAUSSIAN) ph = exp(-e2 * r2);
+            else if (kernel == RBF_MQ) ph = sqrt(1.0 + e2 * r2);
+            else if (kernel == RBF_WENDLAND) {
+                const double q = sqrt(e2 * r2), w = q < 1.0 ? 1.0 - q : 0.0;
+                ph = w * w * w * (3.0 * q + 1.0);
+            } else ph = 1.0 / sqrt(1.0 + e2 * r2);
+            acc += sl[j] * ph;
         }
     }
     if (active) u[q] = acc;
@@ -447,9 +484,12 @@ int rbf_run_p2p_multi(rbf_tree *t, int kernel, double eps, const float *lam_s, i
     rbf_pass_timer tm(t, RBF_PASS_P2P, s);
     double e2 = eps * eps;
     if (kernel == RBF_GAUSSIAN) e2 *= 1.4426950408889634;
-    if (G <= 4) return launch_p2p_multi<4>(t->d, kernel, (float)e2, t, lam_s, G, u, s);
-    if (G <= 8) return launch_p2p_multi<8>(t->d, kernel, (float)e2, t, lam_s, G, u, s);
-    return launch_p2p_multi<16>(t->d, kernel, (float)e2, t, lam_s, G, u, s);
+    return with_kernel(kernel, [&](auto K) {
+        constexpr int KER = decltype(K)::value;
+        if (G <= 4) return launch_p2p_multi<4, KER>(t->d, (float)e2, t, lam_s, G, u, s);
+        if (G <= 8) return launch_p2p_multi<8, KER>(t->d, (float)e2, t, lam_s, G, u, s);
+        return launch_p2p_multi<16, KER>(t->d, (float)e2, t, lam_s, G, u, s);
+    });
 }
 template int rbf_run_p2p<double>(rbf_tree *, int, double, const double *, double *,
                                  cudaStream_t);
@@ -460,7 +500,7 @@ extern "C" int rbf_direct_sum(const double *X, int64_t N, int d, rbf_kernel kern
 {
     RBF_REQUIRE(X && lambda && targets && u, "rbf_direct_sum: NULL pointer");
     RBF_REQUIRE(N >= 1 && d >= 1 && d <= RBF_MAX_DIM && nt >= 0, "rbf_direct_sum: bad sizes");
-    RBF_REQUIRE(kernel == RBF_GAUSSIAN || kernel == RBF_IMQ, "rbf_direct_sum: unknown kernel");
+    RBF_REQUIRE(kernel >= RBF_GAUSSIAN && kernel <= RBF_WENDLAND, "rbf_direct_sum: unknown kernel");
     if (nt == 0) return RBF_OK;
     cudaStream_t s = (cudaStream_t)stream;
     k_direct<<<ceil_div(nt, DS_THREADS), DS_THREADS, 0, s>>>(X, N, d, kernel, eps, lambda, targets,

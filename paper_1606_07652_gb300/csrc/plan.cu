@@ -21,11 +21,7 @@
 
 namespace {
 
-__device__ double phi64(int kernel, double eps, double r2)
-{
-    double e2 = eps * eps * r2;
-    return kernel == RBF_GAUSSIAN ? exp(-e2) : rsqrt(1.0 + e2);
-}
+__device__ double phi64(int kernel, double eps, double r2) { return rbf_phi64(kernel, eps * eps * r2); }
 
 __device__ double taper(double t, double L, double R_in, double alpha)
 {
@@ -168,7 +164,7 @@ void rbf_default_params(rbf_kernel kernel, double side, rbf_fmm_params *p)
 {
     p->M = 32;
     p->period_L = 4.0 * side;
-    p->window_alpha = kernel == RBF_IMQ ? 4.5 : 0.0;
+    p->window_alpha = kernel == RBF_GAUSSIAN ? 0.0 : 4.5;
     p->csample = 1;
     p->grid = RBF_GRID_SHARED;
     p->lagrange_K = 0;
@@ -291,7 +287,9 @@ int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_param
         rbf_default_params(kernel, t->side, &def);
         pp = &def;
     }
-    RBF_REQUIRE(kernel == RBF_GAUSSIAN || kernel == RBF_IMQ, "unknown kernel %d", (int)kernel);
+    RBF_REQUIRE(kernel >= RBF_GAUSSIAN && kernel <= RBF_WENDLAND, "unknown kernel %d", (int)kernel);
+    RBF_REQUIRE(kernel != RBF_MQ || pp->window_alpha > 0.0,
+                "the multiquadric grows with r: window_alpha must be > 0");
     RBF_REQUIRE(eps > 0.0 && std::isfinite(eps), "eps must be positive and finite");
     RBF_REQUIRE(pp->M >= 2 && pp->M <= 64 && pp->M % 2 == 0, "M=%d must be even in [2, 64]", pp->M);
     RBF_REQUIRE(pp->window_alpha >= 0.0, "window_alpha must be >= 0");

@@ -121,7 +121,7 @@ __global__ void k_knn(const double *xs, int64_t N, int d, int D, const double *l
 
 __device__ __forceinline__ double phi64(int kernel, double e2, double r2)
 {
-    return kernel == RBF_GAUSSIAN ? exp(-e2 * r2) : rsqrt(1.0 + e2 * r2);
+    return rbf_phi64(kernel, e2 * r2);
 }
 
 // One warp per listed centre: A_S + delta I (FP64, 32 x 32) in shared memory,

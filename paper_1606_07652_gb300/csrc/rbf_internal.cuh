@@ -91,6 +91,18 @@ __device__ __forceinline__ C cconj(C a)
     return a;
 }
 
+// Phi at (eps r)^2 = e2r2 in FP64, any kernel (rbf_kernel)
+__host__ __device__ inline double rbf_phi64(int kernel, double e2r2)
+{
+    if (kernel == RBF_GAUSSIAN) return exp(-e2r2);
+    if (kernel == RBF_MQ) return sqrt(1.0 + e2r2);
+    if (kernel == RBF_WENDLAND) {
+        const double q = sqrt(e2r2), t = q < 1.0 ? 1.0 - q : 0.0;
+        return t * t * t * (3.0 * q + 1.0);
+    }
+    return 1.0 / sqrt(1.0 + e2r2);
+}
+
 __device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
 

@@ -55,6 +55,8 @@ CASES = [
     ("2d-two-groups-R20", 2, 6000, 2, O.IMQ, 2.0, 16, 4.0, 4.5, 20, "u"),
     ("3d-clustered-ragged-R5", 3, 6000, 2, O.GAUSSIAN, 3.0, 10, 3.0, 0.0, 5, "c"),
     ("2d-small-leaves-R8", 2, 3000, 3, O.IMQ, 2.0, 16, 4.0, 4.5, 8, "u"),
+    ("2d-mq-R6", 2, 6000, 2, O.MQ, 2.0, 16, 4.0, 4.5, 6, "u"),
+    ("3d-wendland-R4", 3, 12000, 2, O.WENDLAND, 0.5, 12, 4.0, 0.0, 4, "u"),
 ]
 
 

@@ -99,6 +99,11 @@ MATVEC_CASES = [
     ("5d", 5, 1500, 2, O.GAUSSIAN, 1.5, 4, 4.0, 0.0, "u"),
     ("4d-depth3-grid", 4, 3000, 3, O.GAUSSIAN, 2.0, 6, 4.0, 0.0, "u"),
     ("6d", 6, 700, 2, O.IMQ, 1.0, 4, 4.0, 4.5, "u"),
+    ("mq-2d", 2, 5000, 4, O.MQ, 2.0, 16, 4.0, 4.5, "u"),
+    ("mq-3d-clustered", 3, 5000, 3, O.MQ, 1.0, 12, 4.0, 4.5, "c"),
+    ("wendland-2d", 2, 5000, 4, O.WENDLAND, 0.5, 16, 4.0, 0.0, "u"),
+    ("wendland-3d-taper", 3, 6000, 3, O.WENDLAND, 3.0, 12, 4.0, 4.5, "u"),
+    ("wendland-1d", 1, 2000, 4, O.WENDLAND, 0.5, 16, 4.0, 0.0, "u"),
 ]
 
 
@@ -160,13 +165,15 @@ def test_multiple_rhs_and_host_entry(rbf):
         assert rel(Uh[c], ref) <= FP64_TOL
 
 
-def test_direct_sum_matches_oracle(rbf):
+@pytest.mark.parametrize("kernel,eps", [(O.IMQ, 2.0), (O.GAUSSIAN, 3.0), (O.MQ, 2.0),
+                                        (O.WENDLAND, 2.5)])
+def test_direct_sum_matches_oracle(rbf, kernel, eps):
     import torch
     X, lam = workloads.uniform(5000, 3, 2)
     tg = np.arange(0, 5000, 37)
-    ref = O.direct(X, lam, O.IMQ, 2.0, tg)
+    ref = O.direct(X, lam, kernel, eps, tg)
     u = torch.empty(len(tg), dtype=torch.float64, device="cuda")
-    rbf.direct_sum(_dev(X), O.IMQ, 2.0, _dev(lam), _dev(tg.astype(np.int64)), u)
+    rbf.direct_sum(_dev(X), kernel, eps, _dev(lam), _dev(tg.astype(np.int64)), u)
     assert rel(u.cpu().numpy(), ref) <= 1e-14
 
 

@@ -132,7 +132,9 @@ def test_poisson_closed_form_coefficients(d):
 # ------------------------------------------------------------ T-SAMP -----
 @pytest.mark.parametrize("kernel,eps,d,M,L,alpha", [(O.IMQ, 2.0, 2, 16, 4.0, 4.5),
                                                     (O.IMQ, 2.0, 3, 12, 4.0, 4.5),
-                                                    (O.GAUSSIAN, 3.0, 3, 10, 3.0, 0.0)])
+                                                    (O.GAUSSIAN, 3.0, 3, 10, 3.0, 0.0),
+                                                    (O.MQ, 2.0, 2, 16, 4.0, 4.5),
+                                                    (O.WENDLAND, 0.5, 2, 16, 4.0, 0.0)])
 def test_sampled_coefficients_interpolate_lattice(kernel, eps, d, M, L, alpha):
     """DFT inversion: with sampled C, K(qh) equals the periodised, windowed sample f(q)
     exactly, and f(q) is Phi(qh) inside the window's flat part."""
@@ -261,6 +263,8 @@ def test_translation_consistency():
     (2, 300, 4, O.IMQ, 2.0, 16, 4.0, 4.5),
     (3, 250, 3, O.IMQ, 2.0, 10, 4.0, 4.5),
     (3, 200, 2, O.GAUSSIAN, 3.0, 12, 3.0, 0.0),
+    (2, 300, 3, O.MQ, 2.0, 16, 4.0, 4.5),
+    (2, 300, 3, O.WENDLAND, 0.5, 16, 4.0, 0.0),
 ])
 def test_fmm_equals_bruteforce(d, N, D, kernel, eps, M, L, alpha):
     """The multilevel FMM (P2M, M2M, M2L over IL_l, L2L, L2P) equals the direct sum of
@@ -309,11 +313,30 @@ def test_direct_sum_small_cases():
     u = O.direct(X, lam, O.IMQ, 2.0)
     q = 1 / np.sqrt(1 + 1.0)
     assert np.allclose(u, [2.0 - q, 2.0 * q - 1.0], rtol=0, atol=1e-15)
+    u = O.direct(X, lam, O.MQ, 2.0)
+    m = np.sqrt(2.0)
+    assert np.allclose(u, [2.0 - m, 2.0 * m - 1.0], rtol=0, atol=1e-15)
+    u = O.direct(X, lam, O.WENDLAND, 0.5)          # eps r = 0.25: 0.75^3 * 1.75
+    w = 0.73828125
+    assert np.allclose(u, [2.0 - w, 2.0 * w - 1.0], rtol=0, atol=1e-15)
+    u = O.direct(X, lam, O.WENDLAND, 2.0)          # eps r = 1: the support edge
+    assert np.allclose(u, [2.0, -1.0], rtol=0, atol=1e-15)
     rng = np.random.default_rng(3)
     Y = rng.random((60, 3))
     A = np.stack([O.direct(Y, e, O.IMQ, 2.0) for e in np.eye(60)], axis=1)
     assert np.allclose(A, A.T, atol=1e-15)
     assert np.max(np.linalg.eigvalsh(A)) <= 60 * 1.0
+
+
+def test_mq_matrix_has_one_positive_eigenvalue():
+    """The multiquadric is conditionally negative definite of order 1 with
+    Phi(0) > 0: its interpolation matrix on distinct centres has exactly one
+    positive eigenvalue (Micchelli), which an IMQ or sign slip would break."""
+    rng = np.random.default_rng(4)
+    Y = rng.random((80, 2))
+    A = np.stack([O.direct(Y, e, O.MQ, 3.0) for e in np.eye(80)], axis=1)
+    ev = np.linalg.eigvalsh(A)
+    assert np.sum(ev > 0) == 1 and np.all(ev[:-1] < 0)
 
 
 # ----------------------------------------------------------- T-GMRES -----
