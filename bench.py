@@ -272,6 +272,8 @@ def run_ours(args):
             out.update(extra_measurements(rbf, tree, Xd, ld, targets, p, kw, dev))
         if args.nested:
             out["nested_grid"] = nested_measurement(rbf, tree, Xd, ld, targets, p, kw, dev)
+        if args.evaluate:
+            out["evaluation"] = evaluation_measurement(rbf, tree, ld, p, kw, dev)
         if args.kernels:
             out["three_kernels"] = kernels_measurement(rbf, dev)
         if args.batch:
@@ -380,6 +382,33 @@ def nested_measurement(rbf, tree, Xd, ld, targets, p, kw, dev, steps=5, K=8):
             "ms_per_step": t, "points_per_s": N / (t / 1e3),
             "rel_err_vs_direct": {"fp32": err(u), "fp64": err(u64)},
             "passes": passes}
+
+
+def evaluation_measurement(rbf, tree, ld, p, kw, dev, nt=1 << 20, steps=5):
+    """The interpolant at nt new uniform points (rbf_eval_*): the one-off set-up
+    (tree over centres and new points) and the FP32 evaluation per call."""
+    import torch
+    Y = torch.as_tensor(np.random.default_rng(404).random((nt, 3)), device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev = rbf.Evaluator(tree, Y)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    s = torch.empty(nt, dtype=torch.float64, device=dev)
+    ev.apply(p["kernel"], p["eps"], ld, s, prec=rbf.FP32, **kw)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ev.apply(p["kernel"], p["eps"], ld, s, prec=rbf.FP32, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ev.free()
+    t = float(np.mean(ms))
+    return {"workload": "2^20 centres (the product's tree) evaluated at %d new uniform points" % nt,
+            "setup_ms": setup_ms, "ms_per_evaluation": t, "new_points_per_s": nt / (t / 1e3)}
 
 
 def kernels_measurement(rbf, dev, n=1 << 20, depths=(4, 5), Ms=(16, 24, 32)):
@@ -649,6 +678,8 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override the number of centres (profiling)")
     ap.add_argument("--batch", type=int, default=1, help="also time the 256-problem batch")
     ap.add_argument("--nested", type=int, default=1, help="also time the nested-grid product")
+    ap.add_argument("--evaluate", type=int, default=1,
+                    help="also time the evaluation at 2^20 new points")
     ap.add_argument("--kernels", type=int, default=1,
                     help="also run the IMQ / MQ / Wendland error-vs-M sweep")
     ap.add_argument("--solve", type=int, default=1, help="also run the solve comparison")

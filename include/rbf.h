@@ -440,6 +440,34 @@ RBF_API int rbf_batch_solve(rbf_batch *b, const double *u_packed, double *lambda
                             void *stream);
 RBF_API void rbf_batch_free(rbf_batch *b);
 
+/* ---------------------------------------------------------------------------
+ * Evaluation at new points: s(y) = sum_j lambda_j Phi(y - x_j) (Eq. (1) with
+ * targets that are not centres, e.g. the interpolant after the solve).
+ * ------------------------------------------------------------------------- */
+typedef struct rbf_eval rbf_eval;
+
+/* Prepare the evaluation of the centres of tree t at nt new points Y (device,
+ * [nt][d] row-major FP64, copied; the tree is only read).  One tree over the
+ * centres and the new points together is built with t's root cube and depth,
+ * so the product runs the same passes (near field over neighbour leaves, far
+ * field through the expansions) with zero coefficients on the new points.
+ * Every point of Y must lie in t's root cube [lo, lo + side]^d (RBF_EINVAL
+ * otherwise: the far-field approximation holds only inside it).  nt >= 1.
+ * *out receives the handle (NULL on failure).  Synchronises `stream`. */
+RBF_API int rbf_eval_create(const rbf_tree *t, const double *Y, int64_t nt, void *stream,
+                            rbf_eval **out);
+
+/* s = the FMM evaluation at the new points for nrhs coefficient columns.
+ * lambda: device FP64, N x nrhs in t's original centre order, leading dimension
+ * ld_lambda >= N; s: device FP64, nt x nrhs, leading dimension ld_s >= nt.
+ * Kernel, eps, params and precision as in rbf_fmm_matvec.  Asynchronous. */
+RBF_API int rbf_eval_apply(rbf_eval *e, rbf_kernel kernel, double eps, const rbf_fmm_params *params,
+                           rbf_precision prec, const double *lambda, int64_t ld_lambda, double *s,
+                           int64_t ld_s, int nrhs, void *stream);
+
+/* Release an evaluation handle (not the source tree).  NULL is accepted. */
+RBF_API void rbf_eval_free(rbf_eval *e);
+
 /* Release a tree and everything it owns.  NULL is accepted. */
 RBF_API void rbf_tree_free(rbf_tree *t);
 

@@ -430,6 +430,20 @@ def fmm(T, lam, kernel: int, eps: float, omegaC, M: int, L: float, return_parts:
     return u
 
 
+def fmm_evaluate(X, lam, Y, lo, side: float, D: int, kernel: int, eps: float, omegaC, M: int,
+                 L: float):
+    """The FMM evaluation at new points Y (Eq. (1) with targets that are not centres):
+    one tree over the centres followed by the new points (root cube [lo, lo+side]^d,
+    depth D), coefficients lambda on the centres and 0 on the new points; the product
+    at the new points.  Returns s[len(Y)]."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    Z = np.concatenate([X, Y])
+    lz = np.concatenate([np.asarray(lam, dtype=np.float64), np.zeros(len(Y))])
+    T = tree(Z, lo, side, D)
+    return fmm(T, lz, kernel, eps, omegaC, M, L)[len(X):]
+
+
 def fmm_brute(T, lam, kernel: int, eps: float, omegaC, M: int, L: float):
     """Tiny-N brute force of what the FMM computes: Phi on near pairs, K on all others."""
     d = T["d"]

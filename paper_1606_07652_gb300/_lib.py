@@ -119,6 +119,11 @@ def load():
                                       _c_vp]
     lib.rbf_precond_build.argtypes = [_c_vp, _c_int, _c_dbl, _c_vp, _c_dbl, _c_vp]
     lib.rbf_precond_apply.argtypes = [_c_vp, _c_vp, _c_vp, _c_vp]
+    lib.rbf_eval_create.argtypes = [_c_vp, _c_vp, _c_i64, _c_vp, P(_c_vp)]
+    lib.rbf_eval_apply.argtypes = [_c_vp, _c_int, _c_dbl, P(FmmParams), _c_int, _c_vp, _c_i64,
+                                   _c_vp, _c_i64, _c_int, _c_vp]
+    lib.rbf_eval_free.argtypes = [_c_vp]
+    lib.rbf_eval_free.restype = None
     lib.rbf_kernel_error.argtypes = [_c_int, _c_dbl, _c_int, P(FmmParams), _c_dbl, _c_int,
                                      P(_c_dbl)]
     lib.rbf_autotune.argtypes = [_c_int, _c_dbl, _c_int, _c_i64, _c_dbl, _c_dbl, P(FmmParams),
@@ -267,6 +272,43 @@ def fmm_matvec(tree: Tree, kernel: int, eps: float, lam, u, prec=FP64, M=None, p
                                  _dev(lam, "float64", "lam"), N, _dev(u, "float64", "u"), N, nrhs,
                                  _stream()), "rbf_fmm_matvec")
     return u
+
+
+class Evaluator:
+    """rbf_eval handle: the FMM evaluation of a tree's centres at new points Y
+    (contiguous float64 CUDA tensor (nt, d) inside the tree's root cube)."""
+
+    def __init__(self, tree: Tree, Y):
+        nt, d = Y.shape
+        h = ctypes.c_void_p()
+        _check(load().rbf_eval_create(tree.handle, _dev(Y, "float64", "Evaluator Y"), nt, _stream(),
+                                      ctypes.byref(h)), "rbf_eval_create")
+        self._h = h
+        self.nt = nt
+        self.side = tree.info()["side"]
+
+    def apply(self, kernel: int, eps: float, lam, s, prec=FP64, M=None, period_L=None,
+              window_alpha=None, csample=1, grid=GRID_SHARED, lagrange_K=0):
+        """rbf_eval_apply: lam float64 CUDA (N,) or (nrhs, N); s float64 CUDA (nt,) or (nrhs, nt)."""
+        nrhs = 1 if lam.dim() == 1 else lam.shape[0]
+        p = _params(M, period_L, window_alpha, csample, kernel, self.side, grid, lagrange_K)
+        _check(load().rbf_eval_apply(self._h, kernel, float(eps),
+                                     ctypes.byref(p) if p is not None else None, prec,
+                                     _dev(lam, "float64", "lam"), lam.shape[-1],
+                                     _dev(s, "float64", "s"), s.shape[-1], nrhs, _stream()),
+               "rbf_eval_apply")
+        return s
+
+    def free(self):
+        if self._h:
+            load().rbf_eval_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def check_device_waits():

@@ -13,7 +13,7 @@
 //        P = K-point Lagrange stencil in xi (child node k/2 for parent node k),
 //        applied one dimension at a time
 //   M2L  Eq. (45) over IL_l(a), written as the children of the parent's
-//        neighbours minus a's own neighbours:
+//        neighbours minus a's own neighbours (the 2^d siblings together):
 //          L_l(a) = omega_l C_l [ sum_{p' in N(par a)} e^{i xi_l.(c_a - c_p')} Vt_p'
 //                                - sum_{b in N(a)} e^{i xi_l.(c_a - c_b)} V_b ],
 //          Vt_p' = sum_{children b} e^{-i xi_l.(c_b - c_p')} V_b  (level-l grid)
@@ -237,57 +237,161 @@ __global__ void __launch_bounds__(kThreads) k_l2l_first(int M, int n1, int64_t n
     *dst = acc;
 }
 
-// M2L of level l (see file header); writes L_l
+constexpr int ipow(int b, int e) { return e <= 0 ? 1 : b * ipow(b, e - 1); }
+
+// One dimension t of a separable offset sum.  in[bs + 2^t (j + W r)], j < W, holds
+// partial sums with the dimensions below t already reduced to the child bit bs;
+// out[bs + 2^t b + 2^(t+1) r] = sum_{e<3} f[b][e] in[bs + 2^t (s + W r)], s = e for
+// the 3 offsets around the parent (W = 3) or s = b + e for the block of 4 around
+// the children (W = 4).
+template <int T, int W, int DIM, typename C>
+__device__ __forceinline__ void sep_step(const C *in, C *out, const C (&f)[2][3])
+{
+    constexpr int NBS = 1 << T;
+    constexpr int NR = ipow(W, DIM - T - 1);
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int bs = 0; bs < NBS; ++bs)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                C acc;
+                acc.x = acc.y = 0;
+#pragma unroll
+                for (int e = 0; e < 3; ++e) cmac(acc, f[b][e], in[bs + NBS * ((W == 3 ? e : b + e) + W * r)]);
+                out[bs + NBS * b + 2 * NBS * r] = acc;
+            }
+}
+
+// Offset sum of one parent's 2^d children: out[b] = sum over the 3^d offsets of
+// prod_t f_t[b_t][e_t] * val(offset), val read from src at the boxes ids[] (-1 =
+// empty), W = 3 (ids = the parent's neighbours, e is the offset) or W = 4 (ids =
+// the 4^d block around the children, child b's neighbour at offset e sits at b + e).
+template <int W, int DIM, typename C>
+__device__ __forceinline__ void offset_sum(const C *src, int64_t ms, int64_t m, const int32_t *ids,
+                                           const C *ph, int n1, const int *kk, int row0, int brow,
+                                           C *out)
+{
+    constexpr int R0 = ipow(W, DIM - 1);
+    C a[2 * R0];
+    C f[2][3];
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) f[b][e] = ph[(row0 + brow * b + e) * n1 + kk[0]];
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+        C v[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int id = ids[j + W * r];
+            if (id >= 0) v[j] = src[(int64_t)id * ms + m];
+            else v[j].x = v[j].y = 0;
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            C acc;
+            acc.x = acc.y = 0;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) cmac(acc, f[b][e], v[W == 3 ? e : b + e]);
+            a[b + 2 * r] = acc;
+        }
+    }
+    if constexpr (DIM == 1) {
+        out[0] = a[0];
+        out[1] = a[1];
+    } else {
+        C g[2][3];
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 3; ++e) g[b][e] = ph[(row0 + brow * b + e) * n1 + kk[1]];
+        if constexpr (DIM == 2) {
+            sep_step<1, W, DIM>(a, out, g);
+        } else {
+            C a1[4 * ipow(W, DIM - 2)];
+            sep_step<1, W, DIM>(a, a1, g);
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int e = 0; e < 3; ++e) g[b][e] = ph[(row0 + brow * b + e) * n1 + kk[2]];
+            sep_step<2, W, DIM>(a1, out, g);
+        }
+    }
+}
+
+// M2L of level l for the 2^d children of every parent p at level l-1 (file
+// header): the 3^d parent-neighbour terms are shared by the siblings, and their
+// own 3^d neighbours all lie in the 4^d block around them; both sums are done
+// one dimension at a time.  Writes L_l of every child.
 template <typename R, int DIM>
-__global__ void __launch_bounds__(kThreads) k_m2l_nest(int M, int n1, int64_t nmode, int64_t ms,
-                                                       const cplx<R> *ph, const uint64_t *key,
-                                                       const int32_t *parent, const int32_t *nbr,
-                                                       const int32_t *pnbr, const cplx<R> *Vt,
-                                                       const cplx<R> *V, const R *wc, cplx<R> *L)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 2 : 1) k_m2l_sib(int M, int n1, int64_t nmode, int64_t ms,
+                                                      const cplx<R> *ph, const int32_t *nb4,
+                                                      const int32_t *pnbr, const cplx<R> *Vt,
+                                                      const cplx<R> *V, const R *wc, cplx<R> *L)
 {
     using C = cplx<R>;
-    constexpr int NQ = DIM == 1 ? 3 : (DIM == 2 ? 9 : 27);
-    const int64_t a = blockIdx.x;
+    constexpr int NB = 1 << DIM, Q3 = ipow(3, DIM), Q4 = ipow(4, DIM);
+    const int64_t p = blockIdx.x;
     const int64_t m = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     if (m >= nmode) return;
     int kk[DIM];
     mode_digits<DIM>(m, n1, M, kk);
-    const unsigned bits = (unsigned)(key[a] & ((1u << DIM) - 1u));
-    C pn[DIM][3], pp[DIM][3];
-#pragma unroll
-    for (int t = 0; t < DIM; ++t) {
-        const unsigned b = (bits >> t) & 1u;
-#pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            pn[t][e] = ph[(kPhNb + e) * n1 + kk[t]];
-            pp[t][e] = ph[(kPhPar + 3 * b + e) * n1 + kk[t]];
-        }
-    }
-    const int32_t *nb = nbr + a * NQ;
-    const int32_t *pb = pnbr + (int64_t)parent[a] * NQ;
-    C sp{(R)0, (R)0}, sn{(R)0, (R)0};
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const int e0 = q % 3, e1 = (q / 3) % 3, e2 = q / 9;
-        const int bp = pb[q], bn = nb[q];
-        if (bp >= 0) {
-            C f = pp[0][e0];
-            if (DIM > 1) f = cmul(f, pp[DIM > 1 ? 1 : 0][e1]);
-            if (DIM > 2) f = cmul(f, pp[DIM > 2 ? 2 : 0][e2]);
-            cmac(sp, f, Vt[(int64_t)bp * ms + m]);
-        }
-        if (bn >= 0) {
-            C f = pn[0][e0];
-            if (DIM > 1) f = cmul(f, pn[DIM > 1 ? 1 : 0][e1]);
-            if (DIM > 2) f = cmul(f, pn[DIM > 2 ? 2 : 0][e2]);
-            cmac(sn, f, V[(int64_t)bn * ms + m]);
-        }
-    }
+    const int32_t *blk = nb4 + p * Q4;
+    C sp[NB], sn[NB];
+    offset_sum<3, DIM>(Vt, ms, m, pnbr + p * Q3, ph, n1, kk, kPhPar, 3, sp);
+    offset_sum<4, DIM>(V, ms, m, blk, ph, n1, kk, kPhNb, 0, sn);
     const R w = wc[m];
-    C out;
-    out.x = w * (sp.x - sn.x);
-    out.y = w * (sp.y - sn.y);
-    L[a * ms + m] = out;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        int q = 0, st = 1;
+#pragma unroll
+        for (int t = 0; t < DIM; ++t) {
+            q += (1 + ((b >> t) & 1)) * st;
+            st *= 4;
+        }
+        const int id = blk[q];
+        if (id >= 0) {
+            C o;
+            o.x = w * (sp[b].x - sn[b].x);
+            o.y = w * (sp[b].y - sn[b].y);
+            L[(int64_t)id * ms + m] = o;
+        }
+    }
+}
+
+// nb4[p][q]: level-l box at block coordinate 2 c_p - 1 + q_t (q = sum_t q_t 4^t, q_t < 4)
+// around the children of parent p (level l-1), -1 where empty or outside
+__global__ void k_build_nb4(const uint64_t *pkey, int np, const uint64_t *key, int nbox, int d, int l,
+                            int nq, int32_t *nb4)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)np * nq) return;
+    const int p = (int)(i / nq);
+    int q = (int)(i % nq);
+    const uint64_t kp = pkey[p];
+    uint64_t nk = 0;
+    bool inside = true;
+    for (int t = 0; t < d; ++t) {
+        int c = 0;
+        for (int bit = 0; bit < l - 1; ++bit) c |= (int)((kp >> (bit * d + t)) & 1u) << bit;
+        const int x = 2 * c - 1 + (q % 4);
+        q /= 4;
+        if (x < 0 || x >= (1 << l)) inside = false;
+        for (int bit = 0; bit < l && inside; ++bit)
+            nk |= (uint64_t)((x >> bit) & 1) << (bit * d + t);
+    }
+    int32_t out = -1;
+    if (inside) {
+        int lo = 0, hi = nbox;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (key[mid] < nk) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo < nbox && key[lo] == nk) out = lo;
+    }
+    nb4[i] = out;
 }
 
 // ------------------------------------------------------------ host tables --
@@ -413,15 +517,27 @@ int build_nested(rbf_tree *t, rbf_plan *p, cudaStream_t s)
         RBF_TRY(rbf_make_omegaC(p->prec, d, p->kernel, p->eps, M, p->L * std::ldexp(1.0, 2 - l),
                                 p->alpha, t->side * std::ldexp(1.0, 2 - l), 1, p->nmode, wc, s));
     }
-    // neighbour tables of levels 1..D
+    // neighbour tables of levels 1..D-1 (the parents' neighbours in M2L)
     int nq = 1;
     for (int q = 0; q < d; ++q) nq *= 3;
-    for (int l = 1; l <= D; ++l) {
+    for (int l = 1; l < D; ++l) {
         const int nb = t->lev[l].nbox;
         RBF_TRY(rbf_alloc(&p->nest_nbr[l], (size_t)std::max(nb, 1) * nq));
         if (nb > 0) {
             k_build_nbr<<<ceil_div((int64_t)nb * nq, 256), 256, 0, s>>>(t->lev[l].key, nb, d, l, nq,
                                                                          p->nest_nbr[l]);
+            RBF_LAUNCH_CHECK();
+        }
+    }
+    // blocks of 4^d boxes around the children of every parent, levels 2..D
+    int nq4 = 1;
+    for (int q = 0; q < d; ++q) nq4 *= 4;
+    for (int l = 2; l <= D; ++l) {
+        const int np = t->lev[l - 1].nbox;
+        RBF_TRY(rbf_alloc(&p->nest_nb4[l], (size_t)std::max(np, 1) * nq4));
+        if (np > 0) {
+            k_build_nb4<<<ceil_div((int64_t)np * nq4, 256), 256, 0, s>>>(
+                t->lev[l - 1].key, np, t->lev[l].key, t->lev[l].nbox, d, l, nq4, p->nest_nb4[l]);
             RBF_LAUNCH_CHECK();
         }
     }
@@ -497,10 +613,9 @@ int run_nested(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStr
     {
         rbf_pass_timer tm(t, RBF_PASS_M2L, s, (D - 1) + (D - 2) * d);
         for (int l = 2; l <= D; ++l) {
-            const rbf_level &lv = t->lev[l];
             C *Ll = l == D ? (C *)p->Lleaf : (C *)p->nest_L[l];
-            k_m2l_nest<R, DIM><<<dim3(lv.nbox, ych), kThreads, 0, s>>>(
-                M, n1, nmode, ms, ph, lv.key, lv.parent, p->nest_nbr[l], p->nest_nbr[l - 1],
+            k_m2l_sib<R, DIM><<<dim3(t->lev[l - 1].nbox, ych), kThreads, 0, s>>>(
+                M, n1, nmode, ms, ph, p->nest_nb4[l], p->nest_nbr[l - 1],
                 (const C *)p->nest_Vt[l - 1], (const C *)p->V[l], (const R *)p->nest_wc[l], Ll);
             RBF_LAUNCH_CHECK();
         }
@@ -551,6 +666,8 @@ void rbf_nested_free(rbf_plan *p)
     for (int l = 0; l <= RBF_MAX_DEPTH; ++l) {
         rbf_free(p->nest_wc[l]);
         rbf_free(p->nest_nbr[l]);
+        rbf_free(p->nest_nb4[l]);
+        p->nest_nb4[l] = nullptr;
         rbf_free(p->nest_Vt[l]);
         rbf_free(p->nest_L[l]);
         p->nest_wc[l] = p->nest_Vt[l] = p->nest_L[l] = nullptr;

@@ -229,7 +229,9 @@ struct rbf_plan {
     void *lag_fw = nullptr;       // [n1][lagK] interpolation weights
     int32_t *lag_tidx = nullptr;  // [n1][lagKT] parent node of each transposed tap
     void *lag_tw = nullptr;       // [n1][lagKT] transposed weights (0 in padding)
-    int32_t *nest_nbr[RBF_MAX_DEPTH + 1] = {nullptr};  // [nbox_l][3^d] neighbours, levels 1..D
+    int32_t *nest_nbr[RBF_MAX_DEPTH + 1] = {nullptr};  // [nbox_l][3^d] neighbours, levels 1..D-1
+    int32_t *nest_nb4[RBF_MAX_DEPTH + 1] = {nullptr};  // [nbox_{l-1}][4^d] level-l boxes around
+                                                       // each parent's children, levels 2..D
     void *nest_Vt[RBF_MAX_DEPTH + 1] = {nullptr};  // parents on their children's grid, 1..D-1
     void *nest_L[RBF_MAX_DEPTH + 1] = {nullptr};   // local expansions, levels 2..D-1 (D: Lleaf)
     void *nest_tmp[2] = {nullptr, nullptr};        // [nleaf][mstride] pass buffers

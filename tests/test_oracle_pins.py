@@ -519,3 +519,41 @@ def test_nested_fmm_converges_to_level_kernels():
         errs.append(np.max(np.abs(u - ud)))
     assert errs[0] > errs[1] >= errs[2] * 0.5
     assert errs[2] <= 1.05 * kerr * np.sum(np.abs(lam))
+
+
+# ------------------------------------------------------ new points -------
+def test_evaluate_at_centres_equals_product():
+    """Evaluating at copies of some centres reproduces the product at those
+    centres: the copies fall in the same boxes, carry zero coefficients and
+    change neither the lists nor any expansion."""
+    rng = np.random.default_rng(12)
+    X = rng.random((500, 2))
+    lam = rng.standard_normal(500)
+    wc = O.coeffs_sampled(O.IMQ, 2.0, 2, 16, 4.0, 4.5, 1.0)
+    T = O.tree(X, np.zeros(2), 1.0, 3)
+    u = O.fmm(T, lam, O.IMQ, 2.0, wc, 16, 4.0)
+    pick = rng.choice(500, 40, replace=False)
+    s = O.fmm_evaluate(X, lam, X[pick], np.zeros(2), 1.0, 3, O.IMQ, 2.0, wc, 16, 4.0)
+    assert np.max(np.abs(s - u[pick])) <= 1e-14 * np.max(np.abs(u))
+
+
+@pytest.mark.parametrize("kernel,eps,alpha", [(O.IMQ, 2.0, 4.5), (O.GAUSSIAN, 3.0, 0.0),
+                                              (O.MQ, 1.0, 4.5)])
+def test_evaluate_within_lemma_bound(kernel, eps, alpha):
+    """At new points the evaluation differs from the direct interpolant
+    sum_j lambda_j Phi(y - x_j) by at most max_far |K - Phi| * sum |lambda|
+    (scaled Lemma, Eq. (33))."""
+    rng = np.random.default_rng(13)
+    X = rng.random((800, 2))
+    Y = rng.random((300, 2))
+    lam = rng.standard_normal(800)
+    M, L = 24, (3.0 if kernel == O.GAUSSIAN else 4.0)
+    wc = O.coeffs_sampled(kernel, eps, 2, M, L, alpha, 1.0)
+    s = O.fmm_evaluate(X, lam, Y, np.zeros(2), 1.0, 3, kernel, eps, wc, M, L)
+    Z = np.concatenate([X, Y])
+    sd = O.direct(Z, np.concatenate([lam, np.zeros(300)]), kernel, eps, np.arange(800, 1100))
+    r = rng.uniform(-1, 1, (6000, 2))
+    r = r[np.max(np.abs(r), axis=1) >= 1.0 / 8]
+    kerr = np.max(np.abs(O.kernel_K(wc, 2, M, L, r) - O.phi(kernel, eps, np.linalg.norm(r, axis=1))))
+    assert np.max(np.abs(s - sd)) <= kerr * np.sum(np.abs(lam))
+    assert np.max(np.abs(s - sd)) > 0.0
