@@ -586,7 +586,7 @@ int run_nested(rbf_tree *t, const rbf_plan *p, const R *lam_s, R *u_far, cudaStr
     RBF_TRY(rbf_run_p2m<R>(t, &leaf, lam_s, (C *)p->V[D], s));
     {
         int launches = 0;
-        for (int l = D; l >= 2; --l) launches += 1 + (l >= 3 ? d : 0);
+        for (int l = D; l >= 2; --l) launches += l < 3 ? 1 : 1 + d;
         rbf_pass_timer tm(t, RBF_PASS_M2M, s, launches);
         for (int l = D; l >= 2; --l) {
             const rbf_level &lc = t->lev[l], &lp = t->lev[l - 1];

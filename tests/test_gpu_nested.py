@@ -6,7 +6,8 @@ in xi, M2L per level with that level's coefficients and L2L by anterpolation
 oracle of ``oracle/nested.py`` on the same tree: FP64 to 1e-12 relative L2,
 FP32 to 5e-6.  The cases span d = 1, 2, 3, several mode chunks per box, both
 kernels, stencils of 4, 8 and 12 points, clustered points (empty boxes,
-ragged leaves) and depth 2 (no interpolation at all).
+ragged leaves), depth 2 (no interpolation at all) and M = 40 (lines of 41
+nodes along each dimension).
 """
 import numpy as np
 import pytest
@@ -55,6 +56,8 @@ CASES = [
     ("3d-depth3-K8", 3, 6000, 3, O.IMQ, 2.0, 16, 8, "u"),
     ("3d-M24-K12", 3, 3000, 3, O.GAUSSIAN, 2.0, 24, 12, "u"),
     ("3d-depth2", 3, 2000, 2, O.IMQ, 2.0, 16, 8, "u"),
+    # 3-D M = 40 (41 nodes per dimension: more than one warp per line)
+    ("3d-M40", 3, 600, 3, O.IMQ, 2.0, 40, 8, "u"),
 ]
 
 
