@@ -134,6 +134,22 @@ def near_pairs(tree):
     return tot
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (the job's time is its slowest rank's);
+    the value itself when not distributed."""
+    if dist is None:
+        return float(value)
+    import torch
+    tt = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(units_per_rank, world, steps, t_max_ms):
+    """Whole-job rate: units every rank processed per step, over the slowest rank's time."""
+    return world * units_per_rank * steps / (t_max_ms / 1e3)
+
+
 def run_ours(args):
     import torch
     import paper_1606_07652_gb300 as rbf
@@ -183,13 +199,9 @@ def run_ours(args):
     rbf.profile(tree, False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_local = float(np.sum(step_ms))
-    t_max = t_local
-    if dist:
-        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t_local, dist, dev)
     ms_per_step = t_max / args.steps
-    value = world * N * args.steps / (t_max / 1e3)
+    value = job_throughput(N, world, args.steps, t_max)
     clocks = clk.summary()
 
     # end to end through the host entry point: pinned host lambda in, host u out
@@ -204,12 +216,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         rbf.fmm_matvec_host(tree, p["kernel"], p["eps"], lam_h, u_h, prec=prec, **kw)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_t = float(np.sum(e2e_ms))
-    if dist:
-        tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_t = float(tt.item())
-    e2e = {"value": world * N * args.steps / (e2e_t / 1e3), "unit": UNIT,
+    e2e_t = max_over_ranks(float(np.sum(e2e_ms)), dist, dev)
+    e2e = {"value": job_throughput(N, world, args.steps, e2e_t), "unit": UNIT,
            "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8}
 
     out = None
