@@ -46,7 +46,6 @@
 
 namespace {
 
-constexpr int kThreads = 256;
 constexpr int kRows = 128;           // tile rows = TMEM lanes
 constexpr int kKS = 8;               // points (P2M) or mode rows (L2P) per stage
 constexpr int kSlots = 6;                      // MMA k-steps per stage
@@ -283,12 +282,20 @@ __device__ __forceinline__ void leaf_centre(const TcArgs &a, int leaf, double *c
 }
 
 // ---------------------------------------------------------- warp roles ----
-constexpr int kProdWarps = 8;                          // warps 0..7: operand producers
-constexpr int kMmaWarp = kProdWarps;                   // warp 8: MMA issue (one lane)
-constexpr int kEpiWarp0 = kProdWarps + 1;              // warps 9..16: accumulator epilogue
+#ifndef RBF_TC_GROUPS
+#define RBF_TC_GROUPS 3
+#endif
+constexpr int kGroups = RBF_TC_GROUPS;                 // producer groups of four warps
+// two and three groups are tested; four (832 threads, 72 registers) ran out a bounded
+// wait in testing with the cause not found, so they are not allowed
+static_assert(kGroups == 2 || kGroups == 3, "RBF_TC_GROUPS must be 2 or 3");
+constexpr int kProdWarps = 4 * kGroups;                // warps 0..4G-1: operand producers
+constexpr int kProdThreads = 32 * kProdWarps;
+constexpr int kMmaWarp = kProdWarps;                   // MMA issue (one lane)
+constexpr int kEpiWarp0 = kProdWarps + 1;              // 8 warps: accumulator epilogue
 constexpr int kEpiWarps = 8;
-constexpr int kCopyWarp = kEpiWarp0 + kEpiWarps;       // warp 17: bulk copies
-constexpr int kTcThreads = 32 * (kCopyWarp + 1);       // 576
+constexpr int kCopyWarp = kEpiWarp0 + kEpiWarps;       // bulk copies
+constexpr int kTcThreads = 32 * (kCopyWarp + 1);
 constexpr int kP2MStages = 4, kL2PStages = 3, kMaxStages = 4;
 constexpr int kRing = 8;                               // copy-slot barriers
 constexpr int kRingE = 8, kRingL = 6;                  // copy slots of P2M, L2P
@@ -518,13 +525,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_p2m_tc(const TcArgs a, const 
     const int eslot = kKS * rowpadE, lslot = kKS * gpad;
     float2 *Er = reinterpret_cast<float2 *>(smem + S * sbytes);       // [kRingE][kKS][rowpadE]
     float *Lr = reinterpret_cast<float *>(Er + kRingE * eslot);        // [kRingE][kKS][gpad]
-    float2 *PF = reinterpret_cast<float2 *>(Lr + kRingE * lslot);      // [2 groups][2][kKS][kPF]
-    int *pfo = reinterpret_cast<int *>(PF + 4 * kKS * kPF);            // [2][kPF][RBF_MAX_DIM]
+    float2 *PF = reinterpret_cast<float2 *>(Lr + kRingE * lslot);      // [groups][2][kKS][kPF]
+    int *pfo = reinterpret_cast<int *>(PF + 2 * kGroups * kKS * kPF);  // [2][kPF][RBF_MAX_DIM]
     const Sync y = sync_at(pfo + 2 * kPF * RBF_MAX_DIM);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntot = a.ncol * a.G;
-    if (tid == 0) sync_init(y, kProdWarps / 2);
+    if (tid == 0) sync_init(y, 4);
     __syncwarp();
     if (warp == 0) tmem_alloc(smem_u32(y.tslot), a.tcols);
     tc_fence_before();
@@ -542,8 +549,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_p2m_tc(const TcArgs a, const 
         const int np = a.leaf_off[leaf + 1] - (int)p0;
         const int nch = (np + kKS - 1) / kKS;
         if (warp < kProdWarps) {
-            // ---- producers: two groups of four warps build alternate stages, so
-            // the latency chains of two stages overlap
+            // ---- producers: groups of four warps build stages in turn, so the
+            // latency chains of several stages overlap
             const int grp = warp >> 2, gt = tid & 127;
             const int rlast = min(row0 + kRows, a.nrow) - 1;
             const int qbase = a.d >= 3 ? row0 / a.n1 : 0;
@@ -557,7 +564,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_p2m_tc(const TcArgs a, const 
             // table offsets of the tile's prefixes, one buffer per item parity (every
             // producer finished the item before last at the previous item's barrier)
             int *pfi = pfo + (nit & 1) * kPF * RBF_MAX_DIM;
-            for (int q = tid; q < npf; q += kThreads) {
+            for (int q = tid; q < npf; q += kProdThreads) {
                 int Q = qbase + q;
                 for (int t = a.d - 3; t >= 1; --t) {
                     pfi[q * RBF_MAX_DIM + t] = a.n0 + (t - 1) * a.n1 + Q % a.n1;
@@ -565,8 +572,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_p2m_tc(const TcArgs a, const 
                 }
                 pfi[q * RBF_MAX_DIM] = Q;
             }
-            named_bar(kBarProd, kThreads);
-            for (int lc = grp; lc < nch; lc += 2) {
+            named_bar(kBarProd, kProdThreads);
+            for (int lc = grp; lc < nch; lc += kGroups) {
                 const int gcc = gc + lc;
                 const int s = gcc % S, k = gcc % kRingE;
                 if (gcc >= S && !*y.abort) (void)wait_or_abort(&y.empty[s], ((gcc - S) / S) & 1, y.abort);
@@ -574,7 +581,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_p2m_tc(const TcArgs a, const 
                 const int cnt = min(kKS, np - lc * kKS);
                 const float2 *Ec = Er + k * eslot;
                 const float *Lc = Lr + k * lslot;
-                float2 *PFc = PF + (grp * 2 + ((lc >> 1) & 1)) * kKS * kPF;
+                float2 *PFc = PF + (grp * 2 + ((lc / kGroups) & 1)) * kKS * kPF;
                 if (!*y.abort)
                     for (int idx = gt; idx < kKS * npf; idx += 128) {
                         const int p = idx / npf, q = idx - p * npf;
@@ -723,7 +730,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_l2p_tc(const TcArgs a, const 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ncolt = Rg * a.ncol;        // columns of the tile
     const int nch = (a.nrow + kKS - 1) / kKS;
-    if (tid == 0) sync_init(y, kProdWarps / 2);
+    if (tid == 0) sync_init(y, 4);
     __syncwarp();
     if (warp == 0) tmem_alloc(smem_u32(y.tslot), a.tcols);
     tc_fence_before();
@@ -746,14 +753,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_l2p_tc(const TcArgs a, const 
             // ---- producers: per-point phases e^{+i xi (x - c)} of the item, then stages
             double c[RBF_MAX_DIM];
             leaf_centre(a, leaf, c);
-            named_bar(kBarProd, kThreads);   // every producer is done with the previous item
-            for (int idx = tid; idx < kRows * a.rowlen; idx += kThreads) {
+            named_bar(kBarProd, kProdThreads);   // every producer is done with the previous item
+            for (int idx = tid; idx < kRows * a.rowlen; idx += kProdThreads) {
                 const int p = idx / a.rowlen, j = idx - p * a.rowlen;
                 E[p * a.rowpad + j] = p < cnt ? table_entry(a, a.xs + p0 + pt0 + p, a.N, j, c, 1.0f)
                                               : make_float2(0.0f, 0.0f);
             }
-            named_bar(kBarProd, kThreads);
-            // two groups of four warps take alternate stages; thread gt of a group
+            named_bar(kBarProd, kProdThreads);
+            // groups of four warps take stages in turn; thread gt of a group
             // owns point gt (all 8 mode rows of a stage) and up to two W rows
             const int grp = warp >> 2, gt = tid & 127;
             const float2 *Ep = E + gt * a.rowpad;
@@ -801,7 +808,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_l2p_tc(const TcArgs a, const 
                 dg[0] = Q;
                 if (grp * kKS < a.nrow) pf = prefix_from_digits();
             }
-            for (int lc = grp; lc < nch; lc += 2) {
+            for (int lc = grp; lc < nch; lc += kGroups) {
                 const int gcc = gc + lc;
                 const int s = gcc % S, k = gcc % kRingL;
                 if (gcc >= S && !*y.abort) (void)wait_or_abort(&y.empty[s], ((gcc - S) / S) & 1, y.abort);
@@ -853,8 +860,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_l2p_tc(const TcArgs a, const 
                     }
                     fence_async_smem();
                 }
-                // skip the other group's stage
-                if (a.d >= 3 && advance(kKS) && (lc + 2) * kKS < a.nrow) pf = prefix_from_digits();
+                // skip the other groups' stages
+                if (a.d >= 3 && advance((kGroups - 1) * kKS) && (lc + kGroups) * kKS < a.nrow)
+                    pf = prefix_from_digits();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&y.full[s]));
             }
@@ -995,7 +1003,7 @@ void p2m_shape(const rbf_tree *t, const rbf_plan *p, int G, int *nth, size_t *sm
     const int gpad = 16;   // coefficient columns of the point-major copy
     *smem = stage_bytes(16 * best_c, kP2MStages) +
             (size_t)kRingE * kKS * (rowpad_even(t, p) * sizeof(float2) + gpad * sizeof(float)) +
-            (size_t)4 * kKS * kPF * sizeof(float2) + (size_t)2 * kPF * RBF_MAX_DIM * sizeof(int) +
+            (size_t)2 * kGroups * kKS * kPF * sizeof(float2) + (size_t)2 * kPF * RBF_MAX_DIM * sizeof(int) +
             kSyncBytes;
 }
 
