@@ -296,7 +296,14 @@ constexpr int kEpiWarp0 = kProdWarps + 1;              // 8 warps: accumulator e
 constexpr int kEpiWarps = 8;
 constexpr int kCopyWarp = kEpiWarp0 + kEpiWarps;       // bulk copies
 constexpr int kTcThreads = 32 * (kCopyWarp + 1);
-constexpr int kP2MStages = 4, kL2PStages = 3, kMaxStages = 4;
+#ifndef RBF_P2M_STAGES
+#define RBF_P2M_STAGES 4
+#endif
+#ifndef RBF_L2P_STAGES
+#define RBF_L2P_STAGES 4
+#endif
+constexpr int kP2MStages = RBF_P2M_STAGES, kL2PStages = RBF_L2P_STAGES;
+constexpr int kMaxStages = kP2MStages > kL2PStages ? kP2MStages : kL2PStages;
 constexpr int kRing = 8;                               // copy-slot barriers
 constexpr int kRingE = 8, kRingL = 6;                  // copy slots of P2M, L2P
 // named barriers (0 = __syncthreads): all producers, epilogue, P2M producer groups
