@@ -471,6 +471,15 @@ RBF_API void rbf_eval_free(rbf_eval *e);
 /* Release a tree and everything it owns.  NULL is accepted. */
 RBF_API void rbf_tree_free(rbf_tree *t);
 
+/* Self-test of the failure path of the bounded device waits: one thread waits,
+ * with the same try-wait loop and backoff as the tensor-core kernels, on an
+ * mbarrier that nothing arrives on, and gives up after `seconds` (0 < seconds
+ * <= 2) of SM clock.  *gave_up_host = 1 when the wait gave up (the expected
+ * outcome); the device status bit it sets makes the next
+ * rbf_check_device_waits return RBF_ETIMEOUT (and clear it).  No fault, no
+ * hang: the kernel returns.  Synchronises `stream`. */
+RBF_API int rbf_selftest_bounded_wait(double seconds, int *gave_up_host, void *stream);
+
 /* Message for a status code, and the detail of the last failure on this thread. */
 RBF_API const char *rbf_strerror(int code);
 RBF_API const char *rbf_last_error(void);

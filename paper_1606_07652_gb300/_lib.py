@@ -94,6 +94,7 @@ def load():
     lib.rbf_fmm_matvec.argtypes = [_c_vp, _c_int, _c_dbl, P(FmmParams), _c_int, _c_vp, _c_i64,
                                    _c_vp, _c_i64, _c_int, _c_vp]
     lib.rbf_check_device_waits.argtypes = []
+    lib.rbf_selftest_bounded_wait.argtypes = [_c_dbl, ctypes.POINTER(_c_int), _c_vp]
     lib.rbf_fmm_matvec_host.argtypes = [_c_vp, _c_int, _c_dbl, P(FmmParams), _c_int, _c_vp,
                                         _c_vp, _c_int, _c_vp]
     lib.rbf_direct_sum.argtypes = [_c_vp, _c_i64, _c_int, _c_int, _c_dbl, _c_vp, _c_vp, _c_i64,
@@ -309,6 +310,14 @@ class Evaluator:
             self.free()
         except Exception:
             pass
+
+
+def selftest_bounded_wait(seconds: float = 0.05) -> int:
+    """rbf_selftest_bounded_wait: 1 when a wait on a barrier that nothing completes gave up."""
+    g = _c_int(0)
+    _check(load().rbf_selftest_bounded_wait(float(seconds), ctypes.byref(g), _stream()),
+           "rbf_selftest_bounded_wait")
+    return g.value
 
 
 def check_device_waits():

@@ -4,6 +4,8 @@
 
 #include <algorithm>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rbf_internal.cuh"
 
 static thread_local char g_last_error[512] = "";
@@ -54,9 +56,17 @@ extern "C" const char *rbf_last_error(void) { return g_last_error; }
 extern "C" const char *rbf_version(void) { return "0.1.0"; }
 
 // ---------------------------------------------------------------- profiling --
+namespace {
+const char *const kPassNames[RBF_PASS_COUNT] = {"rbf P2P", "rbf P2M", "rbf M2M", "rbf M2L",
+                                                "rbf L2P", "rbf permute"};
+}
+
+// Every pass is also an NVTX range (header-only NVTX 3: free unless a profiler
+// that collects ranges is attached).
 rbf_pass_timer::rbf_pass_timer(rbf_tree *t_, int pass_, cudaStream_t s_, int launches)
     : t(t_), pass(pass_), s(s_)
 {
+    nvtxRangePushA(pass >= 0 && pass < RBF_PASS_COUNT ? kPassNames[pass] : "rbf pass");
     if (!t || !t->prof.on) return;
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return;
@@ -67,6 +77,7 @@ rbf_pass_timer::rbf_pass_timer(rbf_tree *t_, int pass_, cudaStream_t s_, int lau
 
 rbf_pass_timer::~rbf_pass_timer()
 {
+    nvtxRangePop();
     if (!t || !t->prof.on) return;
     if (t->prof.stop[pass].size() >= t->prof.start[pass].size()) return;
     cudaEvent_t e;

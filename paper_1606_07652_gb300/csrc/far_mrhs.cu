@@ -1147,6 +1147,56 @@ int rbf_run_far_multi(rbf_tree *t, rbf_plan *p, const float *lam_s, int G, float
     return RBF_OK;
 }
 
+namespace {
+// Failure-path self test: one thread waits, with the try-wait loop of the
+// tensor-core kernels and a limit of limit_cycles, on an mbarrier that nothing
+// arrives on; the wait gives up, sets status bit 2 and the kernel returns.
+__global__ void k_wait_selftest(long long limit_cycles, int *gave_up)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const long long t0 = clock64();
+    int g = 0;
+    while (!mbar_try_wait(b, 0)) {
+        if (clock64() - t0 > limit_cycles) {
+            atomicOr(&g_tc_status, 2u);
+            g = 1;
+            break;
+        }
+        __nanosleep(kBackoffNs);
+    }
+    *gave_up = g;
+}
+}  // namespace
+
+extern "C" int rbf_selftest_bounded_wait(double seconds, int *gave_up_host, void *stream)
+{
+    RBF_REQUIRE(gave_up_host && seconds > 0.0 && seconds <= 2.0,
+                "rbf_selftest_bounded_wait: seconds must be in (0, 2]");
+    int khz = 0, dev = 0;
+    RBF_CUDA_TRY(cudaGetDevice(&dev));
+    RBF_CUDA_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    const long long limit = (long long)(seconds * (double)khz * 1e3);
+    int *flag = nullptr;
+    RBF_TRY(rbf_alloc(&flag, 1));
+    cudaStream_t s = (cudaStream_t)stream;
+    k_wait_selftest<<<1, 32, 0, s>>>(limit, flag);
+    int h = 0;
+    const bool ok = cudaGetLastError() == cudaSuccess &&
+                    cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                    cudaStreamSynchronize(s) == cudaSuccess;
+    rbf_free(flag);
+    if (!ok) {
+        rbf_set_error("rbf_selftest_bounded_wait: CUDA failure");
+        return RBF_ECUDA;
+    }
+    *gave_up_host = h;
+    return RBF_OK;
+}
+
 int rbf_tc_fetch_status(int *flags_host)
 {
     unsigned int v = 0, zero = 0;
