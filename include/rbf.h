@@ -347,6 +347,13 @@ RBF_API int rbf_mlp_gradient(rbf_mlp *net, const float *X, const float *T, int64
 RBF_API int rbf_mlp_train_step(rbf_mlp *net, const float *X, const float *T, int64_t B, float lr,
                                float *loss_host, void *stream);
 RBF_API void rbf_mlp_free(rbf_mlp *net);
+/* Checkpoint: write the network (sizes, FP32 parameters, Adam moments and step)
+ * to `path` as a flat little-endian binary with the header "RBFMLP01"; load it
+ * into a new network (*out; NULL on failure).  A loaded network continues
+ * training exactly where the saved one stopped.  RBF_EINVAL on an unreadable,
+ * truncated or foreign file.  Synchronise the device. */
+RBF_API int rbf_mlp_save(const rbf_mlp *net, const char *path);
+RBF_API int rbf_mlp_load(const char *path, rbf_mlp **out);
 
 typedef struct {
     int n_train;      /* training centres, evenly spaced in Morton order */

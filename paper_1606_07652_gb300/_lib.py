@@ -114,6 +114,8 @@ def load():
     lib.rbf_mlp_gradient.argtypes = [_c_vp, _c_vp, _c_vp, _c_i64, _c_vp, P(ctypes.c_float), _c_vp]
     lib.rbf_mlp_train_step.argtypes = [_c_vp, _c_vp, _c_vp, _c_i64, ctypes.c_float,
                                        P(ctypes.c_float), _c_vp]
+    lib.rbf_mlp_save.argtypes = [_c_vp, ctypes.c_char_p]
+    lib.rbf_mlp_load.argtypes = [ctypes.c_char_p, P(_c_vp)]
     lib.rbf_mlp_free.argtypes = [_c_vp]
     lib.rbf_mlp_free.restype = None
     lib.rbf_precond_train.argtypes = [_c_vp, _c_int, _c_dbl, _c_vp, P(TrainOpts), P(TrainReport),
@@ -494,6 +496,24 @@ class Mlp:
                                          X.shape[0], float(lr), ctypes.byref(loss), _stream()),
                "rbf_mlp_train_step")
         return loss.value
+
+    def save(self, path: str):
+        """rbf_mlp_save: parameters and Adam state to a checkpoint file."""
+        _check(load().rbf_mlp_save(self._h, os.fsencode(path)), "rbf_mlp_save")
+
+    @classmethod
+    def load_checkpoint(cls, path: str) -> "Mlp":
+        """rbf_mlp_load: a new network from a checkpoint file."""
+        h = ctypes.c_void_p()
+        _check(load().rbf_mlp_load(os.fsencode(path), ctypes.byref(h)), "rbf_mlp_load")
+        net = cls.__new__(cls)
+        net._h = h
+        n = _c_i64(0)
+        _check(load().rbf_mlp_num_params(h, ctypes.byref(n)), "rbf_mlp_num_params")
+        with open(path, "rb") as f:
+            dims = np.frombuffer(f.read(8 + 20)[8:], dtype=np.int32)
+        net.d_in, net.width, net.d_out = int(dims[0]), int(dims[1]), int(dims[4])
+        return net
 
     def free(self):
         if self._h:

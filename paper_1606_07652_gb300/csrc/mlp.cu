@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <vector>
 
+#include <cstring>
+
 #include "rbf_internal.cuh"
 
 struct rbf_mlp {
@@ -312,6 +314,79 @@ extern "C" void rbf_mlp_free(rbf_mlp *n)
     rbf_free(n->g1);
     rbf_free(n->part);
     delete n;
+}
+
+// ------------------------------------------------------- checkpoints -----
+// File: "RBFMLP01", int32 dims[5], int64 nparam, int64 Adam step, then the FP32
+// parameters, Adam first and second moments (nparam each), little-endian.
+static const char kMlpMagic[8] = {'R', 'B', 'F', 'M', 'L', 'P', '0', '1'};
+
+extern "C" int rbf_mlp_save(const rbf_mlp *n, const char *path)
+{
+    RBF_REQUIRE(n && path, "rbf_mlp_save: NULL argument");
+    std::vector<float> buf((size_t)n->nparam * 3);
+    RBF_CUDA_TRY(cudaDeviceSynchronize());
+    RBF_CUDA_TRY(cudaMemcpy(buf.data(), n->param, n->nparam * sizeof(float), cudaMemcpyDeviceToHost));
+    RBF_CUDA_TRY(cudaMemcpy(buf.data() + n->nparam, n->m, n->nparam * sizeof(float),
+                            cudaMemcpyDeviceToHost));
+    RBF_CUDA_TRY(cudaMemcpy(buf.data() + 2 * n->nparam, n->v, n->nparam * sizeof(float),
+                            cudaMemcpyDeviceToHost));
+    FILE *f = fopen(path, "wb");
+    RBF_REQUIRE(f != nullptr, "rbf_mlp_save: cannot open %s", path);
+    int32_t dims[5];
+    for (int l = 0; l < 5; ++l) dims[l] = n->dims[l];
+    const int64_t hdr[2] = {n->nparam, n->step};
+    const bool ok = fwrite(kMlpMagic, 1, 8, f) == 8 && fwrite(dims, sizeof(dims), 1, f) == 1 &&
+                    fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+                    fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    const bool closed = fclose(f) == 0;
+    RBF_REQUIRE(ok && closed, "rbf_mlp_save: write to %s failed", path);
+    return RBF_OK;
+}
+
+extern "C" int rbf_mlp_load(const char *path, rbf_mlp **out)
+{
+    RBF_REQUIRE(path && out, "rbf_mlp_load: NULL argument");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    RBF_REQUIRE(f != nullptr, "rbf_mlp_load: cannot open %s", path);
+    char magic[8] = {0};
+    int32_t dims[5] = {0};
+    int64_t hdr[2] = {0, 0};
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMlpMagic, 8) == 0 &&
+              fread(dims, sizeof(dims), 1, f) == 1 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+              dims[1] == dims[2] && dims[2] == dims[3] && hdr[0] > 0 && hdr[1] >= 0;
+    rbf_mlp *n = nullptr;
+    std::vector<float> buf;
+    if (ok && rbf_mlp_create(dims[0], dims[1], dims[4], 0, &n) == RBF_OK && n->nparam == hdr[0]) {
+        buf.resize((size_t)hdr[0] * 3);
+        ok = fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    } else {
+        ok = false;
+    }
+    fclose(f);
+    if (!ok) {
+        rbf_mlp_free(n);
+        rbf_set_error("rbf_mlp_load: %s is not a complete network checkpoint", path);
+        return RBF_EINVAL;
+    }
+    const size_t bytes = (size_t)n->nparam * sizeof(float);
+    int st = RBF_OK;
+    if (cudaMemcpy(n->param, buf.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(n->m, buf.data() + n->nparam, bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(n->v, buf.data() + 2 * n->nparam, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        rbf_set_error("rbf_mlp_load: CUDA copy failed");
+        st = RBF_ECUDA;
+    }
+    n->step = hdr[1];
+    if (st == RBF_OK) st = mlp_refresh_bf16(n, 0);
+    if (st == RBF_OK && cudaDeviceSynchronize() != cudaSuccess) st = RBF_ECUDA;
+    if (st != RBF_OK) {
+        rbf_mlp_free(n);
+        return st;
+    }
+    *out = n;
+    return RBF_OK;
 }
 
 extern "C" int rbf_mlp_num_params(const rbf_mlp *n, int64_t *count)

@@ -181,3 +181,35 @@ def test_precond_apply_matches_oracle(env):
         w = c[i] / (A[i, nb[i]] @ c[i])
         zr[nb[i]] += w * y[i]
     assert rel(z.cpu().numpy(), zr) <= 1e-9
+
+
+def test_network_checkpoint_resumes_training_exactly(env, tmp_path):
+    """rbf_mlp_save / rbf_mlp_load: the reloaded network has the same parameters and
+    Adam state, so further steps give the same losses and parameters bit for bit;
+    truncated and foreign files are rejected."""
+    rbf, _lib, torch = env
+    rng = np.random.default_rng(8)
+    X = torch.as_tensor(rng.standard_normal((256, 96)).astype(np.float32), device="cuda")
+    T = torch.as_tensor(rng.standard_normal((256, 32)).astype(np.float32), device="cuda")
+    a = _lib.Mlp(96, 128, 32, seed=3)
+    for _ in range(5):
+        a.train_step(X, T, 1e-3)
+    path = str(tmp_path / "net.bin")
+    a.save(path)
+    b = _lib.Mlp.load_checkpoint(path)
+    assert (b.d_in, b.width, b.d_out) == (96, 128, 32)
+    assert np.array_equal(a.get_params(), b.get_params())
+    la = [a.train_step(X, T, 1e-3) for _ in range(3)]
+    lb = [b.train_step(X, T, 1e-3) for _ in range(3)]
+    assert la == lb
+    assert np.array_equal(a.get_params(), b.get_params())
+    raw = open(path, "rb").read()
+    bad = tmp_path / "short.bin"
+    bad.write_bytes(raw[: len(raw) // 2])
+    with pytest.raises(rbf.RbfError) as e:
+        _lib.Mlp.load_checkpoint(str(bad))
+    assert e.value.code == -1
+    foreign = tmp_path / "foreign.bin"
+    foreign.write_bytes(b"NOTANMLP" + raw[8:])
+    with pytest.raises(rbf.RbfError):
+        _lib.Mlp.load_checkpoint(str(foreign))
