@@ -1,5 +1,6 @@
 // api.cu -- status codes, error messages and device allocation helpers.
 #include <stdarg.h>
+#include <stdlib.h>
 #include <stdio.h>
 
 #include <algorithm>
@@ -28,6 +29,18 @@ int rbf_malloc(void **p, size_t bytes)
         cudaGetLastError();  // clear the sticky-free allocation error
         rbf_set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? RBF_ENOMEM : RBF_ECUDA;
+    }
+    // test aid: with RBF_POISON set, every allocation starts as all-ones bytes (NaN
+    // in FP32 and FP64), so an entry that is read before it is written shows up
+    if (getenv("RBF_POISON") != nullptr) {
+        e = cudaMemset(*p, 0xFF, bytes);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            cudaFree(*p);
+            *p = nullptr;
+            rbf_set_error("poisoning a new allocation failed: %s", cudaGetErrorString(e));
+            return RBF_ECUDA;
+        }
     }
     return RBF_OK;
 }
