@@ -80,10 +80,11 @@ extern "C" int rbf_eval_create(const rbf_tree *t, const double *Y, int64_t nt, v
     if (st == RBF_OK) {
         double lo[6] = {0, 0, 0, 0, 0, 0};
         for (int q = 0; q < d; ++q) lo[q] = t->lo[q];
-        cudaMemsetAsync(flag, 0, sizeof(int), s);
-        k_combine<<<ceil_div(tot, 256), 256, 0, s>>>(t->xs64, t->perm, t->N, Y, nt, d, lo[0], lo[1],
-                                                     lo[2], lo[3], lo[4], lo[5], t->side, Xc, flag);
-        if (cudaGetLastError() != cudaSuccess ||
+        const bool zeroed = cudaMemsetAsync(flag, 0, sizeof(int), s) == cudaSuccess;
+        if (zeroed)
+            k_combine<<<ceil_div(tot, 256), 256, 0, s>>>(t->xs64, t->perm, t->N, Y, nt, d, lo[0], lo[1],
+                                                         lo[2], lo[3], lo[4], lo[5], t->side, Xc, flag);
+        if (!zeroed || cudaGetLastError() != cudaSuccess ||
             cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             rbf_set_error("rbf_eval_create: CUDA failure while combining the points");
