@@ -22,12 +22,14 @@
 #include "rbf_internal.cuh"
 
 // tuning knobs of the FP32 P2M/L2P tiles: point-loop unroll, resident CTAs per
-// SM, rows per thread, column groups, largest block
+// SM, rows per thread, column groups, largest block, points per shared-memory
+// chunk (five 192-thread CTAs per SM with 52- and 26-point chunks were fastest on
+// the 3-D, M = 32 product)
 #ifndef RBF_FAR_UNROLL
 #define RBF_FAR_UNROLL 1
 #endif
 #ifndef RBF_FAR_MINB
-#define RBF_FAR_MINB 4
+#define RBF_FAR_MINB 5
 #endif
 #ifndef RBF_FAR_RPT
 #define RBF_FAR_RPT 1
@@ -36,7 +38,7 @@
 #define RBF_FAR_NH 2
 #endif
 #ifndef RBF_FAR_BMAX
-#define RBF_FAR_BMAX 256
+#define RBF_FAR_BMAX 192
 #endif
 #ifndef RBF_L2P_MINB
 #define RBF_L2P_MINB RBF_FAR_MINB
@@ -55,8 +57,23 @@
 #ifndef RBF_L2P_SMEMRED
 #define RBF_L2P_SMEMRED 1
 #endif
+#ifndef RBF_FAR_PCH
+#define RBF_FAR_PCH 52
+#endif
+// L2P: five resident CTAs only for narrow column segments (wider ones need the
+// registers of four), and 26-point chunks (five CTAs' shared memory in 3-D at
+// M = 32) only when leaves average at most 32 points, else 32-point chunks
+#ifndef RBF_L2P_NARROW
+#define RBF_L2P_NARROW 36
+#endif
+#ifndef RBF_L2P_MINB_WIDE
+#define RBF_L2P_MINB_WIDE 4
+#endif
+#ifndef RBF_L2P_PCH_BIG
+#define RBF_L2P_PCH_BIG 32
+#endif
 #ifndef RBF_L2P_PCH
-#define RBF_L2P_PCH 32
+#define RBF_L2P_PCH 26
 #endif
 
 namespace {
@@ -281,7 +298,9 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? RBF_FAR_BMAX : 256, sizeof(R)
 
 // ------------------------------------------------------------------ L2P ---
 template <typename R, int NCE, int RPT, int NH>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? RBF_L2P_BMAX : 256, sizeof(R) == 4 ? RBF_L2P_MINB : 1) k_l2p(FarArgs<R> a)
+__global__ void __launch_bounds__(sizeof(R) == 4 ? RBF_L2P_BMAX : 256,
+                                  sizeof(R) == 4 ? (NCE <= RBF_L2P_NARROW ? RBF_L2P_MINB : RBF_L2P_MINB_WIDE) : 1)
+    k_l2p(FarArgs<R> a)
 {
     using C = cplx<R>;
     constexpr int NCH = NCE / NH;
@@ -896,7 +915,9 @@ int launch_p2m_l2p(bool l2p, const FarArgs<R> &a0, int nleaf, cudaStream_t s)
     a.seg = NCE;
     a.seg0 = a.d == 1 ? NCE : even_up(a.n0);
     const int rowlen = a.seg0 + (a.d - 1) * a.seg;
-    a.pch = (int)std::max<int64_t>(1, std::min<int64_t>(l2p && RBF_L2P_SMEMRED ? RBF_L2P_PCH : 64,
+    const bool small_leaves = a.N <= 32 * (int64_t)nleaf;
+    const int l2p_pch = NCE <= RBF_L2P_NARROW && small_leaves ? RBF_L2P_PCH : RBF_L2P_PCH_BIG;
+    a.pch = (int)std::max<int64_t>(1, std::min<int64_t>(l2p && RBF_L2P_SMEMRED ? l2p_pch : RBF_FAR_PCH,
                                                         (64 * 1024) / ((int64_t)rowlen * sizeof(cplx<R>))));
     const int bd = l2p ? pick_block(a.nrow, LRPT, LNH, sizeof(R) == 4 ? RBF_L2P_BMAX : 256)
                        : pick_block(a.nrow, RPT, NH, sizeof(R) == 4 ? RBF_FAR_BMAX : 256);
