@@ -18,18 +18,22 @@
 // E_t[j][k] = e^{-+ i xi_k (x_{j,t} - c_t)}: each thread owns one row and keeps
 // its NC columns in registers, the per-point phase tables sit in shared memory.
 #include <algorithm>
+#include <type_traits>
 
 #include "rbf_internal.cuh"
 
-// tuning knobs of the FP32 P2M/L2P tiles: point-loop unroll, resident CTAs per
-// SM, rows per thread, column groups, largest block, points per shared-memory
-// chunk (five 192-thread CTAs per SM with 52- and 26-point chunks were fastest on
-// the 3-D, M = 32 product)
+// tuning knobs of the FP32 P2M/L2P tiles: point-loop unroll, rows per thread,
+// column groups.  Each kernel is built in two launch shapes, picked per product:
+// "dense" (leaves of up to 96 points on average; for L2P also narrow column
+// segments): five resident CTAs of up to 192 threads per SM, 52-point P2M chunks
+// and, for leaves of up to 32 points, 26-point L2P chunks, so that five CTAs'
+// tables fit in shared memory; "wide": four CTAs of up to 256 threads (192 for
+// column segments wider than 36) and 64- / 32-point chunks, fewer chunks for
+// large leaves.  (Measured: 3-D M = 32 product
+// 16.87 -> 16.54 ms and the 256-problem batch faster with the dense shape; 5-D
+// leaves of 512 points keep the wide one.)
 #ifndef RBF_FAR_UNROLL
 #define RBF_FAR_UNROLL 1
-#endif
-#ifndef RBF_FAR_MINB
-#define RBF_FAR_MINB 5
 #endif
 #ifndef RBF_FAR_RPT
 #define RBF_FAR_RPT 1
@@ -37,48 +41,54 @@
 #ifndef RBF_FAR_NH
 #define RBF_FAR_NH 2
 #endif
-#ifndef RBF_FAR_BMAX
-#define RBF_FAR_BMAX 192
-#endif
-#ifndef RBF_L2P_MINB
-#define RBF_L2P_MINB RBF_FAR_MINB
-#endif
 #ifndef RBF_L2P_RPT
 #define RBF_L2P_RPT RBF_FAR_RPT
 #endif
 #ifndef RBF_L2P_NH
 #define RBF_L2P_NH RBF_FAR_NH
 #endif
-#ifndef RBF_L2P_BMAX
-#define RBF_L2P_BMAX RBF_FAR_BMAX
+#ifndef RBF_DENSE_BMAX
+#define RBF_DENSE_BMAX 192
+#endif
+#ifndef RBF_DENSE_MINB
+#define RBF_DENSE_MINB 5
+#endif
+#ifndef RBF_WIDE_BMAX
+#define RBF_WIDE_BMAX 256
+#endif
+#ifndef RBF_WIDE_MINB
+#define RBF_WIDE_MINB 4
+#endif
+#ifndef RBF_P2M_PCH_DENSE
+#define RBF_P2M_PCH_DENSE 52
+#endif
+#ifndef RBF_P2M_PCH_WIDE
+#define RBF_P2M_PCH_WIDE 64
+#endif
+#ifndef RBF_L2P_PCH_DENSE
+#define RBF_L2P_PCH_DENSE 26
+#endif
+#ifndef RBF_L2P_PCH_WIDE
+#define RBF_L2P_PCH_WIDE 32
+#endif
+#ifndef RBF_L2P_NARROW
+#define RBF_L2P_NARROW 36
 #endif
 // L2P partial sums: 1 = one shared-memory slot per thread and point, reduced
 // once per chunk; 0 = warp shuffles per point
 #ifndef RBF_L2P_SMEMRED
 #define RBF_L2P_SMEMRED 1
 #endif
-#ifndef RBF_FAR_PCH
-#define RBF_FAR_PCH 52
-#endif
-// L2P: five resident CTAs only for narrow column segments (wider ones need the
-// registers of four), and 26-point chunks (five CTAs' shared memory in 3-D at
-// M = 32) only when leaves average at most 32 points, else 32-point chunks
-#ifndef RBF_L2P_NARROW
-#define RBF_L2P_NARROW 36
-#endif
-#ifndef RBF_L2P_MINB_WIDE
-#define RBF_L2P_MINB_WIDE 4
-#endif
-#ifndef RBF_L2P_PCH_BIG
-#define RBF_L2P_PCH_BIG 32
-#endif
-#ifndef RBF_L2P_PCH
-#define RBF_L2P_PCH 26
-#endif
 
 namespace {
 
 constexpr int kFarUnroll = RBF_FAR_UNROLL;
+// largest block of a launch shape: the wide shape keeps 256 threads for narrow
+// column segments and drops to 192 (more registers per thread) for wider ones
+constexpr int far_bmax(bool dense, int nce)
+{
+    return dense ? RBF_DENSE_BMAX : (nce <= RBF_L2P_NARROW ? RBF_WIDE_BMAX : RBF_DENSE_BMAX);
+}
 
 template <typename R>
 struct FarArgs {
@@ -223,8 +233,10 @@ __device__ __forceinline__ void tile_coords(int &g, int &h, int &G)
     G = blockDim.x / NH;
 }
 
-template <typename R, int NCE, int RPT, int NH>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? RBF_FAR_BMAX : 256, sizeof(R) == 4 ? RBF_FAR_MINB : 1) k_p2m(FarArgs<R> a)
+template <typename R, int NCE, int RPT, int NH, bool DENSE>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? far_bmax(DENSE, NCE) : 256,
+                                  sizeof(R) == 4 ? (DENSE ? RBF_DENSE_MINB : RBF_WIDE_MINB) : 1)
+    k_p2m(FarArgs<R> a)
 {
     using C = cplx<R>;
     constexpr int NCH = NCE / NH;
@@ -297,9 +309,9 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? RBF_FAR_BMAX : 256, sizeof(R)
 }
 
 // ------------------------------------------------------------------ L2P ---
-template <typename R, int NCE, int RPT, int NH>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? RBF_L2P_BMAX : 256,
-                                  sizeof(R) == 4 ? (NCE <= RBF_L2P_NARROW ? RBF_L2P_MINB : RBF_L2P_MINB_WIDE) : 1)
+template <typename R, int NCE, int RPT, int NH, bool DENSE>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? far_bmax(DENSE, NCE) : 256,
+                                  sizeof(R) == 4 ? (DENSE ? RBF_DENSE_MINB : RBF_WIDE_MINB) : 1)
     k_l2p(FarArgs<R> a)
 {
     using C = cplx<R>;
@@ -887,15 +899,17 @@ __global__ void __launch_bounds__(256) k_m2l_full(int d, int M, int n1, int64_t 
 // block size: multiple of 32*NH threads, fewest idle row slots
 inline int pick_block(int nrow, int rpt, int nh, int bmax)
 {
+    // a CTA handles one leaf in passes over its mode rows and the resident CTAs per
+    // SM are fixed by the launch bounds, so the block with the fewest passes wins;
+    // among equal counts the smallest (its extra threads would idle)
     const int step = 32 * nh, first = step * ((64 + step - 1) / step);
-    int best = first, best_waste = 1 << 30;
+    int best = first, best_passes = 1 << 30;
     for (int bd = first; bd <= bmax; bd += step) {
         const int per = (bd / nh) * rpt;
         const int passes = (nrow + per - 1) / per;
-        const int waste = passes * per - nrow;
-        if (waste < best_waste || (waste == best_waste && bd > best)) {
+        if (passes < best_passes) {
             best = bd;
-            best_waste = waste;
+            best_passes = passes;
         }
     }
     return best;
@@ -915,22 +929,35 @@ int launch_p2m_l2p(bool l2p, const FarArgs<R> &a0, int nleaf, cudaStream_t s)
     a.seg = NCE;
     a.seg0 = a.d == 1 ? NCE : even_up(a.n0);
     const int rowlen = a.seg0 + (a.d - 1) * a.seg;
-    const bool small_leaves = a.N <= 32 * (int64_t)nleaf;
-    const int l2p_pch = NCE <= RBF_L2P_NARROW && small_leaves ? RBF_L2P_PCH : RBF_L2P_PCH_BIG;
-    a.pch = (int)std::max<int64_t>(1, std::min<int64_t>(l2p && RBF_L2P_SMEMRED ? l2p_pch : RBF_FAR_PCH,
+    // dense shape for leaves of up to 96 points on average (and, for L2P, narrow
+    // column segments); L2P's short chunks only for leaves of up to 32 points
+    const bool dense = sizeof(R) == 4 && a.N <= 96 * (int64_t)nleaf && (!l2p || NCE <= RBF_L2P_NARROW);
+    const bool small = a.N <= 32 * (int64_t)nleaf;
+    const int want = l2p ? (dense && small ? RBF_L2P_PCH_DENSE : RBF_L2P_PCH_WIDE)
+                         : (dense ? RBF_P2M_PCH_DENSE : RBF_P2M_PCH_WIDE);
+    a.pch = (int)std::max<int64_t>(1, std::min<int64_t>(l2p && !RBF_L2P_SMEMRED ? 64 : want,
                                                         (64 * 1024) / ((int64_t)rowlen * sizeof(cplx<R>))));
-    const int bd = l2p ? pick_block(a.nrow, LRPT, LNH, sizeof(R) == 4 ? RBF_L2P_BMAX : 256)
-                       : pick_block(a.nrow, RPT, NH, sizeof(R) == 4 ? RBF_FAR_BMAX : 256);
+    const int bmax = sizeof(R) == 4 ? far_bmax(dense, NCE) : 256;
+    const int bd = l2p ? pick_block(a.nrow, LRPT, LNH, bmax) : pick_block(a.nrow, RPT, NH, bmax);
     size_t smem = (size_t)a.pch * rowlen * sizeof(cplx<R>);
     if (l2p) smem += (size_t)(RBF_L2P_SMEMRED ? bd : bd / 32) * a.pch * sizeof(R);
-    if (l2p) {
-        RBF_CUDA_TRY(cudaFuncSetAttribute(k_l2p<R, NCE, LRPT, LNH>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_l2p<R, NCE, LRPT, LNH><<<nleaf, bd, smem, s>>>(a);
+    auto go = [&](auto shape) -> int {
+        constexpr bool D = decltype(shape)::value;
+        if (l2p) {
+            RBF_CUDA_TRY(cudaFuncSetAttribute(k_l2p<R, NCE, LRPT, LNH, D>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_l2p<R, NCE, LRPT, LNH, D><<<nleaf, bd, smem, s>>>(a);
+        } else {
+            RBF_CUDA_TRY(cudaFuncSetAttribute(k_p2m<R, NCE, RPT, NH, D>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_p2m<R, NCE, RPT, NH, D><<<nleaf, bd, smem, s>>>(a);
+        }
+        return RBF_OK;
+    };
+    if constexpr (sizeof(R) == 4) {
+        RBF_TRY(dense ? go(std::true_type()) : go(std::false_type()));
     } else {
-        RBF_CUDA_TRY(cudaFuncSetAttribute(k_p2m<R, NCE, RPT, NH>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_p2m<R, NCE, RPT, NH><<<nleaf, bd, smem, s>>>(a);
+        RBF_TRY(go(std::false_type()));
     }
     RBF_LAUNCH_CHECK();
     return RBF_OK;
