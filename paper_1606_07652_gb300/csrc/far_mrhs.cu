@@ -282,6 +282,14 @@ __device__ __forceinline__ void leaf_centre(const TcArgs &a, int leaf, double *c
 }
 
 // ---------------------------------------------------------- warp roles ----
+// average points per leaf from which P2M / L2P of several columns run on the
+// tensor cores (measured crossovers)
+#ifndef RBF_TC_P2M_MIN
+#define RBF_TC_P2M_MIN 64
+#endif
+#ifndef RBF_TC_L2P_MIN
+#define RBF_TC_L2P_MIN 96
+#endif
 #ifndef RBF_TC_GROUPS
 #define RBF_TC_GROUPS 3
 #endif
@@ -1086,8 +1094,8 @@ int rbf_run_far_multi(rbf_tree *t, rbf_plan *p, const float *lam_s, int G, float
     size_t smem_p = 0, smem_l = 0;
     p2m_shape(t, p, G, &nth_p, &smem_p);
     l2p_shape(t, p, G, &Rg, &nth_l, &smem_l);
-    const bool tc_p2m = per_leaf >= 64.0 && smem_p <= kSmemMax;
-    const bool tc_l2p = per_leaf >= 96.0 && smem_l <= kSmemMax;
+    const bool tc_p2m = per_leaf >= RBF_TC_P2M_MIN && smem_p <= kSmemMax;
+    const bool tc_l2p = per_leaf >= RBF_TC_L2P_MIN && smem_l <= kSmemMax;
     const int rowpadE = rowpad_even(t, p);
     const int gpad = 16;   // coefficient rows of the point-major copy (G <= 16)
     if (tc_p2m || tc_l2p) {
