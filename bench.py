@@ -229,7 +229,8 @@ def run_ours(args):
         for name, v in prof.items():
             if v["launches"]:
                 passes[name] = {"ms_per_step": v["ms"] / args.steps, "launches": v["launches"]}
-        # algorithmic work per launch ("Roofline")
+        # algorithmic work per launch: P2M/L2P 8 flops per point and mode, M2L one
+        # read and one write of every leaf expansion plus the root, P2P per near pair
         flops_p2m = 8.0 * N * nmode
         bytes_m2l = (2.0 * nleaf + 1.0) * nmode * 8.0
         pairs = near_pairs(tree)

@@ -16,8 +16,8 @@ Layout of the oracle:
 * ``solver.py``: GMRES, the local cardinal solves, k-nearest neighbours and
   the MLP of the learned preconditioner.
 
-Readings of the paper that this oracle fixes (each is also listed in
-DESIGN.md):
+Readings of the paper that this oracle fixes (each is also listed in the
+project's design notes):
 
 * Grid, Sec. 3.2 (the choices after Eq. (P2M)): dxi = 2 pi / L, h = L / M,
   sigma = M dxi / 2 = pi / h.  Nodes xi_k = k dxi, k = -M/2 .. M/2 in every
