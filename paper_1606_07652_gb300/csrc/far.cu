@@ -24,12 +24,12 @@
 
 // tuning knobs of the FP32 P2M/L2P tiles: point-loop unroll, rows per thread,
 // column groups.  Each kernel is built in two launch shapes, picked per product:
-// "dense" (leaves of up to 96 points on average; for L2P also narrow column
-// segments): five resident CTAs of up to 192 threads per SM, 52-point P2M chunks
+// "dense" (leaves of up to 96 points on average and column segments of at most
+// 36): five resident CTAs of up to 192 threads per SM, 52-point P2M chunks
 // and, for leaves of up to 32 points, 26-point L2P chunks, so that five CTAs'
 // tables fit in shared memory; "wide": four CTAs of up to 256 threads (192 for
-// column segments wider than 36) and 64- / 32-point chunks, fewer chunks for
-// large leaves.  (Measured: 3-D M = 32 product
+// column segments wider than 36, three CTAs for segments wider than 52) and
+// 64- / 32-point chunks, fewer chunks for large leaves.  (Measured: 3-D M = 32 product
 // 16.87 -> 16.54 ms and the 256-problem batch faster with the dense shape; 5-D
 // leaves of 512 points keep the wide one.)
 #ifndef RBF_FAR_UNROLL
@@ -89,6 +89,16 @@ constexpr int far_bmax(bool dense, int nce)
 {
     return dense ? RBF_DENSE_BMAX : (nce <= RBF_L2P_NARROW ? RBF_WIDE_BMAX : RBF_DENSE_BMAX);
 }
+// resident CTAs per SM a launch shape is compiled for; the widest column
+// segments (M > 50) drop to three so that their 34 columns per thread stay in
+// registers (four CTAs of 192 threads spilled 192 bytes per thread)
+constexpr int far_minb(bool dense, int nce)
+{
+    return dense ? RBF_DENSE_MINB : (nce <= 52 ? RBF_WIDE_MINB : 3);
+}
+// FP64 column groups: one, except for the widest segments (68 columns of FP64
+// accumulators do not fit in 255 registers)
+constexpr int far_nh64(int nce) { return nce > 52 ? 2 : 1; }
 
 template <typename R>
 struct FarArgs {
@@ -235,7 +245,7 @@ __device__ __forceinline__ void tile_coords(int &g, int &h, int &G)
 
 template <typename R, int NCE, int RPT, int NH, bool DENSE>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? far_bmax(DENSE, NCE) : 256,
-                                  sizeof(R) == 4 ? (DENSE ? RBF_DENSE_MINB : RBF_WIDE_MINB) : 1)
+                                  sizeof(R) == 4 ? far_minb(DENSE, NCE) : 1)
     k_p2m(FarArgs<R> a)
 {
     using C = cplx<R>;
@@ -311,7 +321,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? far_bmax(DENSE, NCE) : 256,
 // ------------------------------------------------------------------ L2P ---
 template <typename R, int NCE, int RPT, int NH, bool DENSE>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? far_bmax(DENSE, NCE) : 256,
-                                  sizeof(R) == 4 ? (DENSE ? RBF_DENSE_MINB : RBF_WIDE_MINB) : 1)
+                                  sizeof(R) == 4 ? far_minb(DENSE, NCE) : 1)
     k_l2p(FarArgs<R> a)
 {
     using C = cplx<R>;
@@ -919,9 +929,9 @@ template <typename R, int NCE>
 int launch_p2m_l2p(bool l2p, const FarArgs<R> &a0, int nleaf, cudaStream_t s)
 {
     constexpr int RPT = sizeof(R) == 4 ? RBF_FAR_RPT : 1;
-    constexpr int NH = sizeof(R) == 4 ? (NCE % (2 * RBF_FAR_NH) == 0 ? RBF_FAR_NH : 2) : 1;
+    constexpr int NH = sizeof(R) == 4 ? (NCE % (2 * RBF_FAR_NH) == 0 ? RBF_FAR_NH : 2) : far_nh64(NCE);
     constexpr int LRPT = sizeof(R) == 4 ? RBF_L2P_RPT : 1;
-    constexpr int LNH = sizeof(R) == 4 ? (NCE % (2 * RBF_L2P_NH) == 0 ? RBF_L2P_NH : 2) : 1;
+    constexpr int LNH = sizeof(R) == 4 ? (NCE % (2 * RBF_L2P_NH) == 0 ? RBF_L2P_NH : 2) : far_nh64(NCE);
     static_assert(NCE % (2 * NH) == 0 && NCE % (2 * LNH) == 0, "column groups must be even");
     // the column segment is read NCE entries wide; all segments of dims >= 1
     // share its length, and dim 0 is the column segment when d == 1
@@ -929,9 +939,10 @@ int launch_p2m_l2p(bool l2p, const FarArgs<R> &a0, int nleaf, cudaStream_t s)
     a.seg = NCE;
     a.seg0 = a.d == 1 ? NCE : even_up(a.n0);
     const int rowlen = a.seg0 + (a.d - 1) * a.seg;
-    // dense shape for leaves of up to 96 points on average (and, for L2P, narrow
-    // column segments); L2P's short chunks only for leaves of up to 32 points
-    const bool dense = sizeof(R) == 4 && a.N <= 96 * (int64_t)nleaf && (!l2p || NCE <= RBF_L2P_NARROW);
+    // dense shape for leaves of up to 96 points on average and column segments of
+    // at most 36 (wider ones spill under its register bound); L2P's short chunks
+    // only for leaves of up to 32 points
+    const bool dense = sizeof(R) == 4 && a.N <= 96 * (int64_t)nleaf && NCE <= RBF_L2P_NARROW;
     const bool small = a.N <= 32 * (int64_t)nleaf;
     const int want = l2p ? (dense && small ? RBF_L2P_PCH_DENSE : RBF_L2P_PCH_WIDE)
                          : (dense ? RBF_P2M_PCH_DENSE : RBF_P2M_PCH_WIDE);
@@ -954,7 +965,7 @@ int launch_p2m_l2p(bool l2p, const FarArgs<R> &a0, int nleaf, cudaStream_t s)
         }
         return RBF_OK;
     };
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (sizeof(R) == 4 && NCE <= RBF_L2P_NARROW) {
         RBF_TRY(dense ? go(std::true_type()) : go(std::false_type()));
     } else {
         RBF_TRY(go(std::false_type()));
