@@ -74,6 +74,12 @@
 #ifndef RBF_L2P_NARROW
 #define RBF_L2P_NARROW 36
 #endif
+// FP32 L2P points per step of the point loop (1 or 2; the tail of an odd count
+// takes the one-point step).  Two: 6.39 -> 6.20 ms at the 3-D M = 32 product.
+// (The same step in P2M spills under the 64-register bound.)
+#ifndef RBF_L2P_POINTS
+#define RBF_L2P_POINTS 2
+#endif
 // L2P partial sums: 1 = one shared-memory slot per thread and point, reduced
 // once per chunk; 0 = warp shuffles per point
 #ifndef RBF_L2P_SMEMRED
@@ -83,6 +89,8 @@
 namespace {
 
 constexpr int kFarUnroll = RBF_FAR_UNROLL;
+constexpr int kL2PPoints = RBF_L2P_POINTS;
+static_assert(kL2PPoints == 1 || kL2PPoints == 2, "RBF_L2P_POINTS must be 1 or 2");
 // largest block of a launch shape: the wide shape keeps 256 threads for narrow
 // column segments and drops to 192 (more registers per thread) for wider ones
 constexpr int far_bmax(bool dense, int nce)
@@ -364,8 +372,59 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? far_bmax(DENSE, NCE) : 256,
                     else Lr[r][q].x = Lr[r][q].y = (R)0;
                 }
             }
+            // adds one point's contribution v of this thread's rows to its partial sum
+            auto deposit = [&](int p, R v) {
+                if (RBF_L2P_SMEMRED) {
+                    part[p * blockDim.x + threadIdx.x] += v;
+                } else {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) part[warp * a.pch + p] += v;
+                }
+            };
+            // Re sum_row A[row] P[row] for one point, P = this thread's column sums
+            auto finish = [&](const C *Ep, const C (&P)[RPT]) {
+                R v = (R)0;
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    if (a.d == 1) {
+                        v += P[r].x;
+                    } else {
+                        const C A = row_factor(Ep, a.d, ro[r]);
+                        v += A.x * P[r].x - A.y * P[r].y;
+                    }
+                }
+                return v;
+            };
+            int p = 0;
+            if (kL2PPoints == 2 && sizeof(R) == 4) {
+                // two points per step: one column sum per point and row, the two
+                // points' FMA chains interleave
+                for (; p + 1 < cnt; p += 2) {
+                    const C *Ea = E + p * rowlen, *Eb = Ea + rowlen;
+                    const C *Ba = Ea + boff + h * NCH, *Bb = Eb + boff + h * NCH;
+                    C Pa[RPT], Pb[RPT];
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) Pa[r].x = Pa[r].y = Pb[r].x = Pb[r].y = (R)0;
+#pragma unroll
+                    for (int q = 0; q < NCH; q += 2) {
+                        C a0, a1, b0, b1;
+                        ld2(Ba + q, a0, a1);
+                        ld2(Bb + q, b0, b1);
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) {
+                            cmac(Pa[r], Lr[r][q], a0);
+                            cmac(Pb[r], Lr[r][q], b0);
+                            cmac(Pa[r], Lr[r][q + 1], a1);
+                            cmac(Pb[r], Lr[r][q + 1], b1);
+                        }
+                    }
+                    deposit(p, finish(Ea, Pa));
+                    deposit(p + 1, finish(Eb, Pb));
+                }
+            }
 #pragma unroll kFarUnroll
-            for (int p = 0; p < cnt; ++p) {
+            for (; p < cnt; ++p) {
                 const C *Ep = E + p * rowlen;
                 const C *B = Ep + boff + h * NCH;
                 // four partial sums per row keep the FMA chains short
@@ -390,23 +449,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? far_bmax(DENSE, NCE) : 256,
                     P[r].x = (P4[r][0].x + P4[r][1].x) + (P4[r][2].x + P4[r][3].x);
                     P[r].y = (P4[r][0].y + P4[r][1].y) + (P4[r][2].y + P4[r][3].y);
                 }
-                R v = (R)0;
-#pragma unroll
-                for (int r = 0; r < RPT; ++r) {
-                    if (a.d == 1) {
-                        v += P[r].x;
-                    } else {
-                        const C A = row_factor(Ep, a.d, ro[r]);
-                        v += A.x * P[r].x - A.y * P[r].y;
-                    }
-                }
-                if (RBF_L2P_SMEMRED) {
-                    part[p * blockDim.x + threadIdx.x] += v;
-                } else {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0) part[warp * a.pch + p] += v;
-                }
+                deposit(p, finish(Ep, P));
             }
         }
         __syncthreads();
