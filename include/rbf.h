@@ -196,7 +196,8 @@ RBF_API int rbf_fmm_matvec_host(rbf_tree *t, rbf_kernel kernel, double eps, cons
                         void *stream);
 
 /* Plain O(N^2) sum of Eq. (1) in FP64 at selected targets (error checks):
- *  X [N][d] row-major, lambda [N], targets [nt] (indices into X), u [nt]. */
+ *  X [N][d] row-major, lambda [N], targets [nt] (indices into X), u [nt].
+ *  A target index outside [0, N) gives NaN in its entry of u. */
 RBF_API int rbf_direct_sum(const double *X, int64_t N, int d, rbf_kernel kernel, double eps,
                    const double *lambda, const int64_t *targets, int64_t nt, double *u, void *stream);
 

@@ -171,6 +171,32 @@ def _dev(t, dtype_name, where):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _rows_cols(a, where):
+    """(rows, length) of a (length,) or (rows, length) array or tensor."""
+    shape = tuple(a.shape)
+    if len(shape) == 1:
+        return 1, shape[0]
+    if len(shape) == 2:
+        return shape[0], shape[1]
+    raise ValueError(f"{where}: expected shape (n,) or (nrhs, n), got {shape}")
+
+
+def _expect(a, shape, where):
+    """The library writes and reads whole blocks through raw pointers, so every
+    buffer's shape is checked here, before any call."""
+    if tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{where}: expected shape {tuple(shape)}, got {tuple(a.shape)}")
+
+
+def _block(tree_n, lam, u, names):
+    """nrhs of a (N,) / (nrhs, N) coefficient block and its equally shaped output."""
+    nrhs, n = _rows_cols(lam, names[0])
+    if n != tree_n:
+        raise ValueError(f"{names[0]}: {n} entries per column, the tree has N={tree_n}")
+    _expect(u, lam.shape, names[1])
+    return nrhs
+
+
 def version() -> str:
     return load().rbf_version().decode()
 
@@ -267,9 +293,10 @@ def fmm_matvec(tree: Tree, kernel: int, eps: float, lam, u, prec=FP64, M=None, p
                window_alpha=None, csample=1, grid=GRID_SHARED, lagrange_K=0):
     """rbf_fmm_matvec: lam, u are float64 CUDA tensors (N,) or (nrhs, N) (rows = columns of
     the column-major N x nrhs block)."""
-    nrhs = 1 if lam.dim() == 1 else lam.shape[0]
-    N = lam.shape[-1]
-    p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"], grid, lagrange_K)
+    info = tree.info()
+    N = info["N"]
+    nrhs = _block(N, lam, u, ("lam", "u"))
+    p = _params(M, period_L, window_alpha, csample, kernel, info["side"], grid, lagrange_K)
     _check(load().rbf_fmm_matvec(tree.handle, kernel, float(eps),
                                  ctypes.byref(p) if p is not None else None, prec,
                                  _dev(lam, "float64", "lam"), N, _dev(u, "float64", "u"), N, nrhs,
@@ -282,18 +309,25 @@ class Evaluator:
     (contiguous float64 CUDA tensor (nt, d) inside the tree's root cube)."""
 
     def __init__(self, tree: Tree, Y):
+        info = tree.info()
+        if Y.dim() != 2 or Y.shape[1] != info["d"]:
+            raise ValueError(f"Evaluator Y: expected shape (nt, {info['d']}), got {tuple(Y.shape)}")
         nt, d = Y.shape
         h = ctypes.c_void_p()
         _check(load().rbf_eval_create(tree.handle, _dev(Y, "float64", "Evaluator Y"), nt, _stream(),
                                       ctypes.byref(h)), "rbf_eval_create")
         self._h = h
         self.nt = nt
-        self.side = tree.info()["side"]
+        self.n = info["N"]
+        self.side = info["side"]
 
     def apply(self, kernel: int, eps: float, lam, s, prec=FP64, M=None, period_L=None,
               window_alpha=None, csample=1, grid=GRID_SHARED, lagrange_K=0):
         """rbf_eval_apply: lam float64 CUDA (N,) or (nrhs, N); s float64 CUDA (nt,) or (nrhs, nt)."""
-        nrhs = 1 if lam.dim() == 1 else lam.shape[0]
+        nrhs, n = _rows_cols(lam, "lam")
+        if n != self.n:
+            raise ValueError(f"lam: {n} entries per column, the tree has N={self.n}")
+        _expect(s, (self.nt,) if lam.dim() == 1 else (nrhs, self.nt), "s")
         p = _params(M, period_L, window_alpha, csample, kernel, self.side, grid, lagrange_K)
         _check(load().rbf_eval_apply(self._h, kernel, float(eps),
                                      ctypes.byref(p) if p is not None else None, prec,
@@ -349,8 +383,9 @@ def fmm_matvec_host(tree: Tree, kernel: int, eps: float, lam_host, u_host=None, 
         lam_host = np.ascontiguousarray(lam_host, dtype=np.float64)
     if u_host is None:
         u_host = np.empty(tuple(lam_host.shape), dtype=np.float64)
-    nrhs = 1 if len(lam_host.shape) == 1 else lam_host.shape[0]
-    p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"], grid, lagrange_K)
+    info = tree.info()
+    nrhs = _block(info["N"], lam_host, u_host, ("lam_host", "u_host"))
+    p = _params(M, period_L, window_alpha, csample, kernel, info["side"], grid, lagrange_K)
     _check(load().rbf_fmm_matvec_host(tree.handle, kernel, float(eps),
                                       ctypes.byref(p) if p is not None else None, prec,
                                       _host_ptr(lam_host, "lam_host"), _host_ptr(u_host, "u_host"),
@@ -376,7 +411,13 @@ def profile_read(tree: Tree) -> dict:
 
 def direct_sum(X, kernel: int, eps: float, lam, targets, u):
     """rbf_direct_sum: X (N, d) float64, lam (N,), targets (nt,) int64, u (nt,) CUDA tensors."""
+    if X.dim() != 2:
+        raise ValueError(f"X: expected shape (N, d), got {tuple(X.shape)}")
     N, d = X.shape
+    _expect(lam, (N,), "lam")
+    if targets.dim() != 1:
+        raise ValueError(f"targets: expected shape (nt,), got {tuple(targets.shape)}")
+    _expect(u, (targets.shape[0],), "u")
     _check(load().rbf_direct_sum(_dev(X, "float64", "X"), N, d, kernel, float(eps),
                                  _dev(lam, "float64", "lam"), _dev(targets, "int64", "targets"),
                                  targets.shape[0], _dev(u, "float64", "u"), _stream()),
@@ -388,10 +429,11 @@ def interp_solve(tree: Tree, kernel: int, eps: float, u, lam, restart_m=50, max_
                  max_refine=10, rtol=1e-8, inner_prec=FP32, precond=0, M=None, period_L=None,
                  window_alpha=None, csample=1, grid=GRID_SHARED, lagrange_K=0):
     """rbf_interp_solve: u, lam float64 CUDA tensors (N,) or (nrhs, N); lam holds the guess."""
-    nrhs = 1 if u.dim() == 1 else u.shape[0]
+    info = tree.info()
+    nrhs = _block(info["N"], u, lam, ("u", "lam"))
     o = SolveOpts(restart_m, max_iters, max_refine, rtol, inner_prec, precond)
     rep = SolveReport()
-    p = _params(M, period_L, window_alpha, csample, kernel, tree.info()["side"], grid, lagrange_K)
+    p = _params(M, period_L, window_alpha, csample, kernel, info["side"], grid, lagrange_K)
     code = load().rbf_interp_solve(tree.handle, kernel, float(eps),
                                    ctypes.byref(p) if p is not None else None,
                                    _dev(u, "float64", "u"), _dev(lam, "float64", "lam"), nrhs,
@@ -409,7 +451,11 @@ def morton_order_noalloc(X, lo, side, depth, perm, keys):
     """rbf_morton_order_noalloc: X (N, d) float64, perm (N,) int32 and keys (N,) uint64 or
     int64 CUDA tensors (written).  Allocates no device memory."""
     import torch
+    if X.dim() != 2:
+        raise ValueError(f"X: expected shape (N, d), got {tuple(X.shape)}")
     N, d = X.shape
+    _expect(perm, (N,), "perm")
+    _expect(keys, (N,), "keys")
     lo_arr = (ctypes.c_double * d)(*[float(v) for v in np.asarray(lo).reshape(d)])
     if perm.dtype != torch.int32 or keys.dtype not in (torch.int64, torch.uint64):
         raise TypeError("morton_order_noalloc: perm must be int32 and keys 64-bit")
@@ -446,6 +492,7 @@ def cardinal_weights(tree: Tree, kernel: int, eps: float, delta_rel: float, cent
 def precond_features(tree: Tree, eps: float, centres, F):
     """rbf_precond_features into the float32 CUDA tensor F of shape (nc, 32 d)."""
     c = np.ascontiguousarray(centres, dtype=np.int64)
+    _expect(F, (len(c), KNN * tree.info()["d"]), "F")
     _check(load().rbf_precond_features(tree.handle, float(eps), _np_ptr(c), len(c),
                                        _dev(F, "float32", "F"), _stream()), "rbf_precond_features")
     return F
@@ -476,14 +523,23 @@ class Mlp:
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)
+        _expect(p, (self.num_params(),), "params")
         _check(load().rbf_mlp_set_params(self._h, _np_ptr(p)), "rbf_mlp_set_params")
 
+    def _rows(self, X, where="X"):
+        if X.dim() != 2 or X.shape[1] != self.d_in:
+            raise ValueError(f"{where}: expected shape (n, {self.d_in}), got {tuple(X.shape)}")
+        return X.shape[0]
+
     def forward(self, X, Y):
+        _expect(Y, (self._rows(X), self.d_out), "Y")
         _check(load().rbf_mlp_forward(self._h, _dev(X, "float32", "X"), X.shape[0],
                                       _dev(Y, "float32", "Y"), _stream()), "rbf_mlp_forward")
         return Y
 
     def gradient(self, X, T, G):
+        _expect(T, (self._rows(X), self.d_out), "T")
+        _expect(G, (self.num_params(),), "G")
         loss = ctypes.c_float(0)
         _check(load().rbf_mlp_gradient(self._h, _dev(X, "float32", "X"), _dev(T, "float32", "T"),
                                        X.shape[0], _dev(G, "float32", "G"), ctypes.byref(loss),
@@ -491,6 +547,7 @@ class Mlp:
         return loss.value
 
     def train_step(self, X, T, lr):
+        _expect(T, (self._rows(X), self.d_out), "T")
         loss = ctypes.c_float(0)
         _check(load().rbf_mlp_train_step(self._h, _dev(X, "float32", "X"), _dev(T, "float32", "T"),
                                          X.shape[0], float(lr), ctypes.byref(loss), _stream()),
@@ -545,6 +602,10 @@ def precond_build(tree: Tree, kernel: int, eps: float, net=None, delta_rel=1e-12
 
 
 def precond_apply(tree: Tree, y, z):
+    """rbf_precond_apply: z = P y for float64 CUDA tensors of shape (N,)."""
+    N = tree.info()["N"]
+    _expect(y, (N,), "y")
+    _expect(z, (N,), "z")
     _check(load().rbf_precond_apply(tree.handle, _dev(y, "float64", "y"), _dev(z, "float64", "z"),
                                     _stream()), "rbf_precond_apply")
     return z
@@ -597,13 +658,21 @@ class Batch:
                                        ctypes.byref(tot)), "rbf_batch_layout")
         return {"off": off, "depth": dep, "M": Ms, "total": tot.value}
 
+    def _packed(self, *named):
+        tot = self.layout()["total"]
+        for a, where in named:
+            if a.numel() != tot:
+                raise ValueError(f"{where}: {a.numel()} entries, the batch packs {tot}")
+
     def matvec(self, lam, u, prec=FP32):
         """rbf_batch_matvec on packed float64 CUDA tensors of layout()["total"] entries."""
+        self._packed((lam, "lam"), (u, "u"))
         _check(load().rbf_batch_matvec(self._h, prec, _dev(lam, "float64", "lam"),
                                        _dev(u, "float64", "u"), _stream()), "rbf_batch_matvec")
         return u
 
     def solve(self, u, lam, restart_m=30, max_iters=100, rtol=1e-6, prec=FP32):
+        self._packed((u, "u"), (lam, "lam"))
         nsys = sum(int(q.get("nrhs", 1)) for q in self.problems)
         rr = np.empty(nsys, np.float64)
         it = _c_int(0)

@@ -433,7 +433,10 @@ __global__ void __launch_bounds__(DS_THREADS) k_direct(const double *X, int64_t 
     const int64_t q = (int64_t)blockIdx.x * DS_THREADS + threadIdx.x;
     double xt[RBF_MAX_DIM];
     const bool active = q < nt;
-    const int64_t ti = active ? targets[q] : 0;
+    int64_t ti = active ? targets[q] : 0;
+    // a target index outside [0, N) reads nothing and gives NaN
+    const bool valid = ti >= 0 && ti < N;
+    if (!valid) ti = 0;
     for (int t = 0; t < d; ++t) xt[t] = active ? X[ti * d + t] : 0.0;
     const double e2 = eps * eps;
     double acc = 0.0;
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(DS_THREADS) k_direct(const double *X, int64_t 
             acc += sl[j] * ph;
         }
     }
-    if (active) u[q] = acc;
+    if (active) u[q] = valid ? acc : __longlong_as_double(0x7ff8000000000000LL);
 }
 
 }  // namespace
