@@ -177,6 +177,20 @@ def test_direct_sum_matches_oracle(rbf, kernel, eps):
     assert rel(u.cpu().numpy(), ref) <= 1e-14
 
 
+def test_direct_sum_out_of_range_targets_give_nan(rbf):
+    """The kernel checks each target index: -1 and N read nothing and give NaN,
+    the valid targets around them are unaffected."""
+    import torch
+    X, lam = workloads.uniform(3000, 2, 4)
+    tg = np.array([5, -1, 17, 3000, 2999], dtype=np.int64)
+    u = torch.empty(len(tg), dtype=torch.float64, device="cuda")
+    rbf.direct_sum(_dev(X), O.IMQ, 2.0, _dev(lam), _dev(tg), u)
+    got = u.cpu().numpy()
+    assert np.isnan(got[1]) and np.isnan(got[3])
+    ok = np.array([0, 2, 4])
+    assert rel(got[ok], O.direct(X, lam, O.IMQ, 2.0, tg[ok])) <= 1e-14
+
+
 def test_auto_box_and_bad_arguments(rbf):
     import torch
     X, lam = workloads.uniform(1000, 2, 5)
