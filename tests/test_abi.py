@@ -50,3 +50,32 @@ def test_argument_errors_need_no_device(lib):
     assert lib.rbf_tree_build(None, 10, 2, None, 1.0, 2, None, ctypes.byref(out)) == -1
     assert lib.rbf_fmm_matvec(None, 0, 1.0, None, 0, None, 0, None, 0, 1, None) == -1
     assert lib.rbf_tree_get_info(None, None) == -1
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/rbf.h compiles as strict ISO C99 (-pedantic -Werror), and a C
+    program taking the address of every declared entry point links against
+    librbf.so: the boundary needs no C++ and no torch."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    from paper_1606_07652_gb300 import _lib
+    names = _declared()
+    src = tmp_path / "abi.c"
+    src.write_text('#include "rbf.h"\n#include <stdio.h>\n\nint main(void)\n{\n'
+                   "    typedef void (*any_fn)(void);\n    any_fn fns[] = {\n"
+                   + ",\n".join(f"        (any_fn){n}" for n in names)
+                   + "\n    };\n    printf(\"%d\\n\", (int)(sizeof(fns) / sizeof(fns[0])));\n"
+                   "    return 0;\n}\n")
+    obj, exe = tmp_path / "abi.o", tmp_path / "abi"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-I" + os.path.join(ROOT, "include"), "-c", str(src), "-o", str(obj)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    libdir = os.path.dirname(_lib.library_path())
+    r = subprocess.run([gcc, str(obj), "-L" + libdir, "-lrbf",
+                        "-Wl,--unresolved-symbols=ignore-in-shared-libs", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
