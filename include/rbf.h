@@ -169,7 +169,8 @@ RBF_API int rbf_tree_export_level(rbf_tree *t, int level, uint64_t *box_key, int
  *  u        device FP64, N x nrhs column-major, leading dimension ld_u; written.
  *  prec     RBF_FP64 or RBF_FP32 arithmetic for every pass.
  *  params   expansion parameters (see rbf_fmm_params); NULL = defaults
- *           (M=32, L=4 side, alpha=4.5 for IMQ, 0 for Gaussian, csample=1).
+ *           (M=32, L=4 side, alpha=0 for the Gaussian and 4.5 for the other
+ *           kernels, csample=1, shared grid).
  * Coefficient tables and expansion workspace are built on first use and kept
  * in the tree until the parameters change.  Asynchronous.
  * With RBF_FP32 and nrhs >= RBF_MULTI_RHS_MIN the columns go through the far
