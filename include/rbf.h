@@ -211,7 +211,7 @@ RBF_API int rbf_direct_sum(const double *X, int64_t N, int d, rbf_kernel kernel,
  *  inner_prec  arithmetic of the matvec inside GMRES (RBF_FP64 or RBF_FP32).
  *  precond     0: none (the diagonal of A is Phi(0) = 1, so the diagonal
  *              preconditioner is the identity); 1: learned sparse approximate
- *              inverse (set with rbf_precond_set). */
+ *              inverse (built with rbf_precond_build). */
 typedef struct {
     int restart_m;
     int max_iters;
@@ -399,10 +399,12 @@ RBF_API int rbf_kernel_error(rbf_kernel kernel, double eps, int d, const rbf_fmm
                              double side, int depth, double *max_err_host);
 
 /* Pick the tree depth (about 32 points per leaf for d >= 3, 64 for d <= 2,
- * depth >= 2), the period and taper (Gaussian: Phi(L - side) < tol / 100;
- * inverse multiquadric: L = 4 side, alpha = 4.5) and the smallest even
- * M in [8, 64] whose measured far-kernel error (rbf_kernel_error) is <= tol
- * (64 when none is).  *err_out (may be NULL) receives the achieved error. */
+ * depth >= 2), the period and taper (Gaussian: no taper, Phi(L - side) <
+ * tol / 100; Wendland: no taper, L just above side + 1/eps so that the support
+ * never wraps; inverse multiquadric and multiquadric: L = 4 side,
+ * alpha = 4.5) and the smallest even M in [8, 64] whose measured far-kernel
+ * error (rbf_kernel_error) is <= tol (64 when none is).  *err_out (may be
+ * NULL) receives the achieved error. */
 RBF_API int rbf_autotune(rbf_kernel kernel, double eps, int d, int64_t N, double side, double tol,
                          rbf_fmm_params *params_out, int *depth_out, double *err_out);
 
