@@ -145,6 +145,13 @@ def max_over_ranks(value, dist, device):
     return float(tt.item())
 
 
+def pg_timeout(args):
+    """Process-group timeout: a rank that fails or leaves makes the others' next
+    collective raise after this long instead of waiting for the library default."""
+    import datetime
+    return datetime.timedelta(seconds=float(getattr(args, "pg_timeout", 600.0)))
+
+
 def job_throughput(units_per_rank, world, steps, t_max_ms):
     """Whole-job rate: units every rank processed per step, over the slowest rank's time."""
     return world * units_per_rank * steps / (t_max_ms / 1e3)
@@ -162,7 +169,7 @@ def run_ours(args):
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group("nccl", timeout=pg_timeout(args))
     dev = torch.device("cuda", local)
     X, lam, targets, p = workloads.config2(n=args.n) if args.n else workloads.config2()
     N = len(X)
@@ -684,6 +691,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=60.0)
+    ap.add_argument("--pg-timeout", type=float, default=600.0,
+                    help="seconds before a collective waiting on a lost rank raises (N > 1)")
     ap.add_argument("--n", type=int, default=0, help="override the number of centres (profiling)")
     ap.add_argument("--batch", type=int, default=1, help="also time the 256-problem batch")
     ap.add_argument("--nested", type=int, default=1, help="also time the nested-grid product")

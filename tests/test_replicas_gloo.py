@@ -52,3 +52,46 @@ def test_single_process_helpers():
     import bench
     assert bench.max_over_ranks(7.5, None, None) == 7.5
     assert bench.job_throughput(2 ** 20, 1, 10, 169.0) == pytest.approx(10 * 2 ** 20 / 0.169)
+
+
+def _leaving_worker(rank, world, port, q):
+    import datetime
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=15))
+    import bench
+    if rank == 1:
+        # leaves between steps: joined the group, no collective of its own in flight
+        q.put((rank, "left"))
+        q.close()
+        q.join_thread()          # the message is sent before the abrupt exit
+        os._exit(3)
+    try:
+        bench.max_over_ranks(100.0, dist, torch.device("cpu"))
+        q.put((rank, "no error"))
+    except Exception:
+        q.put((rank, "error"))
+
+
+def test_lost_rank_fails_the_collective_instead_of_hanging():
+    """A rank that exits between steps: the remaining rank's all-reduce of the
+    timed totals raises (closed connection or the process-group timeout), so the
+    job ends with an error instead of waiting forever."""
+    import time
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_leaving_worker, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+    assert out == {0: "error", 1: "left"}
+    assert procs[1].exitcode == 3
+    assert time.time() - t0 < 110
