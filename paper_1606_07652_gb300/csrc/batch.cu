@@ -390,7 +390,9 @@ static int batch_matvec(rbf_batch *b, int prec, cudaStream_t s)
         RBF_CUDA_TRY(cudaStreamSynchronize(s));
         cudaStream_t cs;
         RBF_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        RBF_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+        const cudaError_t eb = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+        if (eb != cudaSuccess) cudaStreamDestroy(cs);
+        RBF_CUDA_TRY(eb);
         const int st = batch_enqueue(b, prec, cs);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(cs, &g);
