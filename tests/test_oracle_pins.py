@@ -412,6 +412,44 @@ def test_oracle_knn_by_hand():
     assert nb[4].tolist()[0] == 4
 
 
+def test_oracle_features_by_hand():
+    """T-FEAT: eps (x_j - x_i) over the neighbour list, nearest first, flattened."""
+    from oracle.solver import features, knn
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 2.0]])
+    nb = knn(X, 3)
+    assert nb.tolist() == [[0, 1, 2], [1, 0, 2], [2, 0, 1]]
+    F = features(X, nb, 0.5)
+    assert F.tolist() == [[0.0, 0.0, 0.5, 0.0, 0.0, 1.0],
+                          [0.0, 0.0, -0.5, 0.0, -0.5, 1.0],
+                          [0.0, 0.0, 0.0, -1.0, 0.5, -1.0]]
+
+
+def test_oracle_adam_closed_forms():
+    """T-ADAM (Kingma & Ba): with bias-corrected moments a constant gradient g moves
+    every parameter by lr g / (|g| + eps) per step, whatever the step count; and
+    two steps with gradients g1, g2 follow the moments written out by hand."""
+    from oracle.solver import adam_step
+    g = np.array([2.0, -0.5, 1e-3, 0.0])
+    p = np.zeros(4)
+    m = np.zeros(4)
+    v = np.zeros(4)
+    lr, eps = 1e-2, 1e-8
+    for t in range(1, 6):
+        adam_step(p, g, m, v, t, lr)
+        assert np.allclose(p, -t * lr * g / (np.abs(g) + eps), rtol=1e-12, atol=0)
+    g1, g2 = np.array([1.0, -3.0]), np.array([-2.0, 1.0])
+    p = np.array([0.5, 0.5])
+    m = np.zeros(2)
+    v = np.zeros(2)
+    adam_step(p, g1, m, v, 1, lr)
+    adam_step(p, g2, m, v, 2, lr)
+    m2 = 0.9 * 0.1 * g1 + 0.1 * g2                   # first moment after two steps
+    v2 = 0.999 * 0.001 * g1 ** 2 + 0.001 * g2 ** 2   # second moment
+    step2 = lr * (m2 / (1 - 0.9 ** 2)) / (np.sqrt(v2 / (1 - 0.999 ** 2)) + eps)
+    step1 = lr * g1 / (np.abs(g1) + eps)
+    assert np.allclose(p, 0.5 - step1 - step2, rtol=1e-13, atol=0)
+
+
 def test_bf16_rounding_by_hand():
     """BF16 keeps 8 significant bits, ties to even: 1 + 2^-8 (a tie) -> 1; 1 + 3*2^-8 -> 1 + 2^-6;
     1 + 2^-7 is representable."""
