@@ -388,6 +388,23 @@ def test_oracle_mlp_gradient_matches_finite_differences():
         assert abs((lp - lm) / (2 * h) - gb[l][0]) <= 1e-6 * max(1e-3, abs(gb[l][0]))
 
 
+def test_oracle_mlp_forward_by_hand():
+    """T-MLP: three ReLU layers and a linear output, W_l (out x in), worked by hand
+    (a dropped bias, a ReLU on the output or a transposed weight changes the result)."""
+    from oracle.solver import mlp_forward
+    W = [np.array([[1.0, 0.0], [0.0, 1.0], [1.0, 1.0]]),
+         np.eye(3),
+         np.array([[1.0, 1.0, 0.0], [0.0, 0.0, 1.0], [-1.0, 0.0, 0.0]]),
+         np.array([[1.0, 0.0, 2.0], [0.0, 1.0, 0.0]])]
+    b = [np.array([0.0, 0.0, -1.0]), np.array([-0.5, 0.0, 0.0]), np.zeros(3), np.array([0.5, -2.5])]
+    X = np.array([[1.0, 2.0], [-1.0, -1.0]])
+    Y, (h, z) = mlp_forward(W, b, X)
+    # row 0: h1 = (1, 2, 2), h2 = (0.5, 2, 2), h3 = (2.5, 2, 0), y = (3.0, -0.5)
+    # row 1: every hidden unit is cut by the ReLU, y = b_3 (negative entry kept)
+    assert Y.tolist() == [[3.0, -0.5], [0.5, -2.5]]
+    assert h[1].tolist()[0] == [1.0, 2.0, 2.0] and h[3].tolist()[0] == [2.5, 2.0, 0.0]
+
+
 def test_oracle_cardinal_coefficients_are_cardinal():
     """T-CARD: sum_{j in S} c_j Phi(x_k - x_j) = delta_{k, centre} for k in S."""
     from oracle.solver import knn, cardinal
