@@ -203,8 +203,9 @@ def version() -> str:
 
 def _params(M=None, period_L=None, window_alpha=None, csample=1, kernel=GAUSSIAN, side=1.0,
             grid=GRID_SHARED, lagrange_K=0):
-    if M is None and period_L is None and window_alpha is None and grid == GRID_SHARED:
-        return None
+    if (M is None and period_L is None and window_alpha is None and grid == GRID_SHARED
+            and int(csample) == 1 and not lagrange_K):
+        return None            # the library's defaults
     p = FmmParams()
     p.M = 32 if M is None else int(M)
     p.period_L = 4.0 * side if period_L is None else float(period_L)

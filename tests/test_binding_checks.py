@@ -112,3 +112,16 @@ def test_preconditioner_and_network_shapes():
         net.train_step(X, torch.zeros((10, 31), dtype=torch.float32), 1e-3)
     with pytest.raises(TypeError):
         net.forward(X, torch.zeros((10, 32), dtype=torch.float32))
+
+
+def test_parameter_block():
+    """No explicit parameter: NULL (the library's defaults).  Any explicit one,
+    including csample=0 alone, gives a full block with the same defaults filled in."""
+    assert _lib._params() is None
+    p = _lib._params(csample=0, kernel=_lib.GAUSSIAN, side=2.0)
+    assert p is not None and p.csample == 0
+    assert (p.M, p.period_L, p.window_alpha, p.grid) == (32, 8.0, 0.0, _lib.GRID_SHARED)
+    q = _lib._params(M=16, kernel=_lib.IMQ)
+    assert (q.M, q.period_L, q.window_alpha, q.csample) == (16, 4.0, 4.5, 1)
+    n = _lib._params(grid=_lib.GRID_NESTED, lagrange_K=6, kernel=_lib.MQ)
+    assert (n.grid, n.lagrange_K, n.window_alpha) == (_lib.GRID_NESTED, 6, 4.5)
