@@ -272,21 +272,24 @@ RBF_API int rbf_profile_read(rbf_tree *t, double *ms_host, int64_t *launches_hos
  * whole device.
  * It computes exactly what rbf_tree_build stores as keys and perm (same box
  * coordinates, Morton keys and stable (key, index) radix sort), with every
- * temporary buffer (the lower corner, the second key/index buffer, digit
- * histograms, scan partial sums) in one file-scope device arena of fixed size
- * (54,528,256 bytes, 52 MiB), which every GPU that loads the library holds until the
+ * temporary buffer (the second key/index buffer, digit histograms, scan
+ * partial sums) in one file-scope device arena of fixed size (54,528,000
+ * bytes, 52 MiB), which every GPU that loads the library holds until the
  * process exits.
  *  X         device [N][d] row-major FP64, caller's order.
  *  N         1 .. 4,194,304 (= 2^22, the arena's limit); larger N returns
  *            RBF_EINVAL with a message.
  *  d, depth  as rbf_tree_build (depth >= 0, d*depth <= 63).
- *  lo_host   host array of d doubles (root cube corner); side > 0.
+ *  lo_host   host array of d doubles (root cube corner), read during the
+ *            call and passed to the device by value; side > 0.
  *  perm      device int32[N], written: sorted position -> original index.
  *  keys      device uint64[N], written: Morton keys in sorted order.
  * Asynchronous on `stream`; it allocates no memory and calls no allocating
- * library routine.  The first call on a device looks up the arena's device
- * address (cudaGetSymbolAddress) and caches it; make that first call before
- * any stream capture.  Every call shares the one arena, and each region of it
+ * library routine.  The first call in each CUDA context of a device (the
+ * primary context, and again after a cudaDeviceReset) looks up the arena's
+ * device address with that device current (cudaGetSymbolAddress) and caches
+ * it for that context; make that first call before any stream capture.
+ * Every call shares the one arena, and each region of it
  * is fully rewritten before it is read, so the previous call's contents never
  * leak into a result; calls that overlap in time on the GPU (different
  * streams or threads) race on the arena and must be serialised by the caller. */

@@ -7,6 +7,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda.h>
+
 #include "rbf_internal.cuh"
 
 namespace {
@@ -42,11 +44,11 @@ __device__ __forceinline__ int32_t find_key(const uint64_t *keys, int32_t n, uin
 // ---------------------------------------------------------------- keys ----
 // k_t = min(max(floor(((x_t - lo_t)/side) * 2^D), 0), 2^D - 1) in IEEE FP64
 // (explicit round-to-nearest intrinsics: no contraction into FMA).
-__global__ void k_keys(const double *X, int64_t N, int d, int D, const double *lo, double side,
-                       uint64_t *keys, int32_t *idx)
+// Morton key of point i: box coordinates floor((x - lo) / side * 2^D) in FP64,
+// clamped to [0, 2^D - 1] (points on the upper face go to the last box).
+__device__ __forceinline__ uint64_t point_key(const double *X, int64_t i, int d, int D,
+                                              const double *lo, double side)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
     int64_t k[RBF_MAX_DIM];
     double scale = (double)((int64_t)1 << D);
     int64_t kmax = ((int64_t)1 << D) - 1;
@@ -59,7 +61,30 @@ __global__ void k_keys(const double *X, int64_t N, int d, int D, const double *l
         else q = (int64_t)f;
         k[t] = q;
     }
-    keys[i] = morton_encode(k, d, D);
+    return morton_encode(k, d, D);
+}
+
+__global__ void k_keys(const double *X, int64_t N, int d, int D, const double *lo, double side,
+                       uint64_t *keys, int32_t *idx)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    keys[i] = point_key(X, i, d, D, lo, side);
+    idx[i] = (int32_t)i;
+}
+
+// The root cube's lower corner passed by value (kernel parameter space), for
+// callers that hold it only in host memory.
+struct corner_t {
+    double v[RBF_MAX_DIM];
+};
+
+__global__ void k_keys_corner(const double *X, int64_t N, int d, int D, corner_t lo, double side,
+                              uint64_t *keys, int32_t *idx)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    keys[i] = point_key(X, i, d, D, lo.v, side);
     idx[i] = (int32_t)i;
 }
 
@@ -729,8 +754,7 @@ constexpr int64_t NOALLOC_L1 = (NOALLOC_HIST + SCAN_TILE - 1) / SCAN_TILE;
 static_assert(NOALLOC_L1 <= SCAN_TILE, "two scan levels must cover the histogram");
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
-constexpr size_t OFF_LO = 0;
-constexpr size_t OFF_KEYS = OFF_LO + align256(RBF_MAX_DIM * sizeof(double));
+constexpr size_t OFF_KEYS = 0;
 constexpr size_t OFF_VALS = OFF_KEYS + align256(NOALLOC_MAX_N * sizeof(uint64_t));
 constexpr size_t OFF_HIST = OFF_VALS + align256(NOALLOC_MAX_N * sizeof(int32_t));
 constexpr size_t OFF_OFFS = OFF_HIST + align256(NOALLOC_HIST * sizeof(int32_t));
@@ -741,22 +765,65 @@ constexpr size_t ARENA_BYTES = OFF_BOFF + align256(NOALLOC_L1 * sizeof(int32_t))
 // The arena: every GPU that loads the library holds it until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_arena[ARENA_BYTES];
 
-std::mutex g_arena_mu;
-void *g_arena_dev[256] = {nullptr};
+// Driver calls that identify the current context, fetched through the runtime
+// so that the library need not link libcuda.
+using ctx_get_current_fn = CUresult (*)(CUcontext *);
+using ctx_get_id_fn = CUresult (*)(CUcontext, unsigned long long *);
 
-// Device address of the arena on the current device, looked up once per device.
+std::mutex g_arena_mu;
+struct arena_slot {
+    unsigned long long ctx_id = 0;  // 0: not looked up yet (context ids start at 1)
+    void *addr = nullptr;
+};
+arena_slot g_arena_dev[256];
+
+// Id of the context current on this thread (0 if none).
+int current_context_id(unsigned long long *id)
+{
+    static ctx_get_current_fn get_current = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        RBF_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                      cudaEnableDefault, &q1));
+        RBF_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000,
+                                                      cudaEnableDefault, &q2));
+        RBF_REQUIRE(q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess && f1 &&
+                        f2,
+                    "driver entry points cuCtxGetCurrent/cuCtxGetId unavailable");
+        get_current = reinterpret_cast<ctx_get_current_fn>(f1);
+        get_id = reinterpret_cast<ctx_get_id_fn>(f2);
+    }
+    CUcontext ctx = nullptr;
+    RBF_REQUIRE(get_current(&ctx) == CUDA_SUCCESS, "cuCtxGetCurrent failed");
+    *id = 0;
+    if (ctx) RBF_REQUIRE(get_id(ctx, id) == CUDA_SUCCESS, "cuCtxGetId failed");
+    return RBF_OK;
+}
+
+// Device address of the arena in the current device's current context.  It is
+// looked up (cudaGetSymbolAddress, with that device current) on the first call
+// in each context and cached; a new context on the same device (after
+// cudaDeviceReset) has a new id and is looked up again.
 int arena_address(unsigned char **out)
 {
     int dev = 0;
     RBF_CUDA_TRY(cudaGetDevice(&dev));
     RBF_REQUIRE(dev >= 0 && dev < 256, "device ordinal %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_arena_mu);
-    if (!g_arena_dev[dev]) {
+    unsigned long long id = 0;
+    RBF_TRY(current_context_id(&id));
+    arena_slot &slot = g_arena_dev[dev];
+    if (id == 0 || slot.ctx_id != id) {
         void *p = nullptr;
-        RBF_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_arena));
-        g_arena_dev[dev] = p;
+        RBF_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_arena));  // makes the context current
+        RBF_TRY(current_context_id(&id));
+        RBF_REQUIRE(id != 0, "no current CUDA context after cudaGetSymbolAddress");
+        slot.ctx_id = id;
+        slot.addr = p;
     }
-    *out = static_cast<unsigned char *>(g_arena_dev[dev]);
+    *out = static_cast<unsigned char *>(slot.addr);
     return RBF_OK;
 }
 
@@ -793,16 +860,17 @@ extern "C" int rbf_morton_order_noalloc(const double *X, int64_t N, int d, const
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *arena = nullptr;
     RBF_TRY(arena_address(&arena));
-    double *lo_d = reinterpret_cast<double *>(arena + OFF_LO);
     uint64_t *kalt = reinterpret_cast<uint64_t *>(arena + OFF_KEYS);
     int32_t *valt = reinterpret_cast<int32_t *>(arena + OFF_VALS);
     int32_t *hist = reinterpret_cast<int32_t *>(arena + OFF_HIST);
     int32_t *offs = reinterpret_cast<int32_t *>(arena + OFF_OFFS);
     int32_t *bsum = reinterpret_cast<int32_t *>(arena + OFF_BSUM);
     int32_t *boff = reinterpret_cast<int32_t *>(arena + OFF_BOFF);
-    // every arena region below is fully written before it is read
-    RBF_CUDA_TRY(cudaMemcpyAsync(lo_d, lo_host, d * sizeof(double), cudaMemcpyHostToDevice, s));
-    k_keys<<<ceil_div(N, 256), 256, 0, s>>>(X, N, d, depth, lo_d, side, keys, perm);
+    // every arena region below is fully written before it is read; the corner
+    // travels by value in the launch, so no host memory is read after this call
+    corner_t lo{};
+    for (int t = 0; t < d; ++t) lo.v[t] = lo_host[t];
+    k_keys_corner<<<ceil_div(N, 256), 256, 0, s>>>(X, N, d, depth, lo, side, keys, perm);
     RBF_LAUNCH_CHECK();
     const int nbits = d * depth;
     const int nblk = (int)((N + RS_TILE - 1) / RS_TILE);

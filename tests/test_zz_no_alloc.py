@@ -57,6 +57,20 @@ def test_two_calls_match_tree_build(env):
         assert np.array_equal(keys, ref_keys)
 
 
+def test_depth_zero_and_single_centre(env):
+    """No radix pass runs when there are no key bits (depth 0) or one centre:
+    the keys and the identity order then come straight from the key kernel."""
+    rbf, _lib, torch = env
+    X0, _ = workloads.uniform(5000, 3, 43)
+    X1 = np.array([[0.25, 0.75, 0.5]])
+    X1b = np.array([[0.9, 0.1]])
+    for X, d, depth in ((X0, 3, 0), (X1, 3, 4), (X1b, 2, 0), (X0, 3, 0)):
+        perm, keys = _noalloc(_lib, torch, X, d, depth)
+        ref_perm, ref_keys = _reference(rbf, torch, X, d, depth)
+        assert np.array_equal(perm, ref_perm)
+        assert np.array_equal(keys, ref_keys)
+
+
 def test_size_limit_is_rejected(env):
     rbf, _lib, torch = env
     X = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
