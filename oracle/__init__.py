@@ -91,7 +91,10 @@ def num_threads() -> int:
 
 
 def _p(a):
-    return ctypes.c_void_p(a.ctypes.data)
+    # data_as keeps a reference to the array inside the pointer object, so a
+    # temporary (a converted copy built in the argument list) stays alive for
+    # the duration of the call
+    return a.ctypes.data_as(ctypes.c_void_p)
 
 
 _I = ctypes.c_int
