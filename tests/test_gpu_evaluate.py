@@ -11,6 +11,7 @@ import pytest
 
 import oracle as O
 import workloads
+from _parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -28,10 +29,6 @@ def rbf():
 def _dev(a):
     import torch
     return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
-
-
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 CASES = [

@@ -14,6 +14,7 @@ import pytest
 
 import oracle as O
 import workloads
+from _parity import rel
 from oracle import nested as ON
 
 pytestmark = pytest.mark.gpu
@@ -35,10 +36,6 @@ def rbf():
 def _dev(a):
     import torch
     return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
-
-
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def _clustered(n, d, seed):
