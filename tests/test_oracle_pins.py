@@ -420,6 +420,65 @@ def test_oracle_cardinal_coefficients_are_cardinal():
         assert np.max(np.abs(A @ c[i] - e)) < 1e-10
 
 
+def test_oracle_cardinal_regularised_by_hand():
+    """T-CARD with regularisation: c = (A_S + delta I)^-1 e_1, delta = delta_rel ||A_S||_F,
+    on three 1-D centres (0, 1/2, 1), Gaussian eps = 1, inverted by cofactors written out.
+    A delta of delta_rel alone, a norm other than Frobenius, or a shift of the first
+    diagonal entry only each miss these values."""
+    from oracle.solver import cardinal
+    X = np.array([[0.0], [0.5], [1.0]])
+    a, b = np.exp(-0.25), np.exp(-1.0)            # Phi(1/2), Phi(1)
+    fro = np.sqrt(3.0 + 4.0 * a * a + 2.0 * b * b)  # ||A_S||_F, the same for both orders
+    delta_rel = 0.05
+    s = 1.0 + delta_rel * fro
+
+    def first_column_of_inverse(m):
+        c11 = m[1][1] * m[2][2] - m[1][2] * m[2][1]
+        c12 = -(m[1][0] * m[2][2] - m[1][2] * m[2][0])
+        c13 = m[1][0] * m[2][1] - m[1][1] * m[2][0]
+        det = m[0][0] * c11 + m[0][1] * c12 + m[0][2] * c13
+        return np.array([c11, c12, c13]) / det
+
+    want0 = first_column_of_inverse([[s, a, b], [a, s, a], [b, a, s]])  # S = (0, 1, 2)
+    want1 = first_column_of_inverse([[s, a, a], [a, s, b], [a, b, s]])  # S = (1, 0, 2)
+    c = cardinal(X, np.array([[0, 1, 2], [1, 0, 2]]), O.GAUSSIAN, 1.0, delta_rel)
+    assert np.allclose(c[0], want0, rtol=1e-13, atol=0)
+    assert np.allclose(c[1], want1, rtol=1e-13, atol=0)
+    assert not np.allclose(c[0], first_column_of_inverse([[1 + delta_rel, a, b], [a, 1 + delta_rel, a],
+                                                         [b, a, 1 + delta_rel]]), rtol=1e-6)
+
+
+def test_oracle_mlp_bf16_branch_by_hand():
+    """T-MLP with BF16 operands (q = bf16_round): a 2 -> 2 -> 1 network worked by hand.
+    Operands round to 8 significant bits: 1.007 -> 129/128, 1.01 -> 129/128,
+    0.3 -> 77/256, 2.003 -> 2, 0.7 -> 179/256, -1.3 -> -83/64; the biases and the sums
+    stay FP64.  Backward: g = 2 (y - t) / y.size, each product again on rounded
+    operands, ReLU mask from z."""
+    from oracle.solver import bf16_round, mlp_backward, mlp_forward
+    W = [np.array([[1.01, -0.5], [0.3, 2.003]]), np.array([[0.7, -1.3]])]
+    b = [np.array([0.1, -0.9]), np.array([0.05])]
+    X = np.array([[1.007, 0.25]])
+    Y, cache = mlp_forward(W, b, X, q=bf16_round)
+    x0, w11, w21 = 129 / 128, 129 / 128, 77 / 256
+    z1 = np.array([x0 * w11 - 0.125 + 0.1, x0 * w21 + 0.5 - 0.9])   # second unit < 0
+    assert np.allclose(cache[1][0], z1[None], rtol=1e-15, atol=1e-16)
+    h1 = 127 / 128                 # bf16(0.99071...) = 1.984375 / 2
+    y = h1 * (179 / 256) + 0.05
+    assert abs(Y[0, 0] - y) <= 1e-15
+    T = np.array([[0.5]])
+    gW, gb = mlp_backward(W, b, cache, Y, T, q=bf16_round)
+    g = 2.0 * (y - 0.5)                          # 0.48751..., bf16 -> 125/256
+    assert abs(gb[1][0] - g) <= 1e-15
+    assert np.allclose(gW[1], [[(125 / 256) * h1, 0.0]], rtol=1e-15, atol=0)
+    g0 = (125 / 256) * (179 / 256)               # back through bf16 W_2; unit 2 masked
+    assert np.allclose(gb[0], [g0, 0.0], rtol=1e-15, atol=0)
+    gq = 175 / 512                               # bf16(g0)
+    assert np.allclose(gW[0], [[gq * x0, gq * 0.25], [0.0, 0.0]], rtol=1e-15, atol=0)
+    # the identity branch differs in the fourth significant digit
+    Yi, _ = mlp_forward(W, b, X)
+    assert abs(Yi[0, 0] - y) > 1e-4
+
+
 def test_oracle_knn_by_hand():
     """Neighbour order with an exact distance tie broken by index."""
     from oracle.solver import knn
