@@ -35,7 +35,6 @@ sys.path.insert(0, ROOT)
 METRIC = "FMM matvec throughput, 3D N=2^20 IMQ eps=2 (FP32 product)"
 UNIT = "points/s"
 FP32_LANES_PER_SM = 128
-N_SM = 152
 
 
 def _peaks():
@@ -49,9 +48,22 @@ def _peaks():
             "source": "fallback"}
 
 
-def fp32_peak_tflops(sm_mhz):
-    """FP32 FMA peak from unit counts: 152 SMs x 128 lanes x 2 flop x clock."""
-    return N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz, n_sm):
+    """FP32 FMA peak from unit counts: SMs x 128 lanes x 2 flop x clock (context only;
+    the fractions use the measured rates of measured_unit_peaks)."""
+    return n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_unit_peaks(rbf, seconds=0.4):
+    """Issue rates of the arithmetic units measured on this device by the library's own
+    probe (rbf_peak_probe): FP32 and FP64 FMA in TFLOP/s, MUFU ex2 and rsqrt in T results/s."""
+    from paper_1606_07652_gb300 import _lib
+    return {"fp32_tflops": _lib.peak_probe(_lib.PROBE_FFMA, seconds) / 1e12,
+            "fp64_tflops": _lib.peak_probe(_lib.PROBE_DFMA, seconds) / 1e12,
+            "mufu_ex2_tops": _lib.peak_probe(_lib.PROBE_EX2, seconds) / 1e12,
+            "mufu_rsqrt_tops": _lib.peak_probe(_lib.PROBE_RSQRT, seconds) / 1e12,
+            "source": "rbf_peak_probe: 32 warps per SM of independent FFMA / DFMA / "
+                      "ex2.approx / rsqrt.approx chains, CUDA events, %.1f s each" % seconds}
 
 
 class ClockSampler:
@@ -175,6 +187,8 @@ def run_ours(args):
     N = len(X)
     Xd = torch.as_tensor(X, device=dev)
     ld = torch.as_tensor(lam, device=dev)
+    unit_peaks = measured_unit_peaks(rbf) if rank == 0 else None
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     tree = rbf.tree_build(Xd, lo=np.zeros(3), side=1.0, depth=p["depth"])
     info = tree.info()
     kw = dict(M=p["M"], period_L=p["L"], window_alpha=p["alpha"])
@@ -241,8 +255,7 @@ def run_ours(args):
         flops_p2m = 8.0 * N * nmode
         bytes_m2l = (2.0 * nleaf + 1.0) * nmode * 8.0
         pairs = near_pairs(tree)
-        sm_peak_mhz = peaks["sm_max_mhz"]
-        fp32_peak = fp32_peak_tflops(sm_peak_mhz)
+        fp32_peak = unit_peaks["fp32_tflops"]
         work = {
             "p2m": ("alu", flops_p2m / 1e12, fp32_peak, "TFLOP/s"),
             "l2p": ("alu", flops_p2m / 1e12, fp32_peak, "TFLOP/s"),
@@ -259,6 +272,17 @@ def run_ours(args):
                 ach = amount / (ms / 1e3)
                 passes[name].update({"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                                      "frac": ach / peak})
+        if "p2p" in passes:
+            # one rsqrt per pair (IMQ) on the multi-function unit beside ~11 FP32 flops:
+            # the pass is bound by whichever unit its work fills first
+            ms = passes["p2p"]["ms_per_step"]
+            f_fma = 11.0 * pairs / (ms / 1e3) / 1e12 / fp32_peak
+            f_mufu = pairs / (ms / 1e3) / 1e12 / unit_peaks["mufu_rsqrt_tops"]
+            passes["p2p"].update({"frac_fp32": f_fma, "frac_mufu": f_mufu,
+                                  "mufu_achieved_tops": pairs / (ms / 1e3) / 1e12,
+                                  "mufu_peak_tops": unit_peaks["mufu_rsqrt_tops"],
+                                  "binding_unit": "fp32" if f_fma >= f_mufu else "mufu",
+                                  "frac": max(f_fma, f_mufu)})
         dom = max((k for k in passes if k in work), key=lambda k: passes[k]["ms_per_step"])
         d = passes[dom]
         per_launch_ms = prof[dom]["ms"] / prof[dom]["launches"]
@@ -266,7 +290,7 @@ def run_ours(args):
         roof = {"kernel": dom, "bound": d["bound"],
                 "achieved": work[dom][1] / launches_per_step / (per_launch_ms / 1e3),
                 "peak": d["peak"], "unit": d["unit"],
-                "peak_source": ("FP32 FMA peak from unit counts at %g MHz" % sm_peak_mhz
+                "peak_source": ("of measured FP32 FMA rate (rbf_peak_probe)"
                                 if d["bound"] == "alu" else "of %s HBM copy bandwidth"
                                 % peaks["source"]),
                 "traffic": _traffic(dom)}
@@ -283,9 +307,11 @@ def run_ours(args):
                           "parallelism": "replicas" if world > 1 else "single GPU",
                           "l2": "256 MB buffer written between timed steps"},
                "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roof,
-               "passes": passes}
+               "passes": passes,
+               "unit_peaks": dict(unit_peaks, fp32_unit_count_tflops=fp32_peak_tflops(
+                   peaks["sm_max_mhz"], n_sm), n_sm=n_sm)}
         if not args.skip_extra:
-            out.update(extra_measurements(rbf, tree, Xd, ld, targets, p, kw, dev))
+            out.update(extra_measurements(rbf, tree, Xd, ld, targets, p, kw, dev, unit_peaks))
         if args.nested:
             out["nested_grid"] = nested_measurement(rbf, tree, Xd, ld, targets, p, kw, dev)
         if args.evaluate:
@@ -308,8 +334,9 @@ def run_ours(args):
     return out
 
 
-def extra_measurements(rbf, tree, Xd, ld, targets, p, kw, dev):
-    """FP64 product throughput and the error of both products against the FP64 direct sum."""
+def extra_measurements(rbf, tree, Xd, ld, targets, p, kw, dev, unit_peaks):
+    """FP64 product throughput (with its P2M/L2P fractions of the measured FP64 FMA rate)
+    and the error of both products against the FP64 direct sum."""
     import torch
     N = ld.shape[0]
     u32 = torch.empty_like(ld)
@@ -318,11 +345,24 @@ def extra_measurements(rbf, tree, Xd, ld, targets, p, kw, dev):
     rbf.fmm_matvec(tree, p["kernel"], p["eps"], ld, u64, prec=rbf.FP64, **kw)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rbf.profile(tree, True)
     e0.record()
     rbf.fmm_matvec(tree, p["kernel"], p["eps"], ld, u64, prec=rbf.FP64, **kw)
     e1.record()
     torch.cuda.synchronize()
     ms64 = e0.elapsed_time(e1)
+    prof = rbf.profile_read(tree)
+    rbf.profile(tree, False)
+    nmode = (p["M"] // 2 + 1) * (p["M"] + 1) ** 2
+    fp64_passes = {}
+    for name, v in prof.items():
+        if v["launches"]:
+            fp64_passes[name] = {"ms": v["ms"]}
+            if name in ("p2m", "l2p"):
+                tf = 8.0 * N * nmode / (v["ms"] / 1e3) / 1e12
+                fp64_passes[name].update({"achieved_tflops": tf,
+                                          "peak_tflops": unit_peaks["fp64_tflops"],
+                                          "frac": tf / unit_peaks["fp64_tflops"]})
     tg = torch.as_tensor(np.asarray(targets, dtype=np.int64), device=dev)
     ud = torch.empty(len(targets), dtype=torch.float64, device=dev)
     rbf.direct_sum(Xd, p["kernel"], p["eps"], ld, tg, ud)
@@ -335,7 +375,8 @@ def extra_measurements(rbf, tree, Xd, ld, targets, p, kw, dev):
                 "max_abs": float(np.max(np.abs(v - ud))),
                 "max_rel_to_max": float(np.max(np.abs(v - ud)) / np.max(np.abs(ud)))}
 
-    return {"fp64": {"value": N / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64},
+    return {"fp64": {"value": N / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                     "passes": fp64_passes},
             "error_vs_direct_4096_targets": {"fp32": err(u32), "fp64": err(u64)}}
 
 

@@ -263,6 +263,22 @@ RBF_API int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps, const r
 RBF_API int rbf_profile(rbf_tree *t, int enable);
 RBF_API int rbf_profile_read(rbf_tree *t, double *ms_host, int64_t *launches_host);
 
+/* Measured peak rate of one arithmetic unit of the current device (the
+ * denominators of roofline fractions; the paper has no counterpart).  A grid
+ * of 32 warps per SM runs independent dependency chains of one instruction:
+ *  RBF_PROBE_FFMA   FP32 fused multiply-add, in flop/s (2 per FMA)
+ *  RBF_PROBE_DFMA   FP64 fused multiply-add, in flop/s
+ *  RBF_PROBE_EX2    ex2.approx.f32 on the multi-function unit, results/s
+ *  RBF_PROBE_RSQRT  rsqrt.approx.f32 on the multi-function unit, results/s
+ * seconds (0, 10]: length of the timed launch (after a short calibration).
+ * rate_host: the measured rate.  Synchronises `stream`; allocates a small
+ * output buffer for the duration of the call. */
+#define RBF_PROBE_FFMA 0
+#define RBF_PROBE_DFMA 1
+#define RBF_PROBE_EX2 2
+#define RBF_PROBE_RSQRT 3
+RBF_API int rbf_peak_probe(int kind, double seconds, double *rate_host, void *stream);
+
 /* Morton order of the centres without any device allocation.  The paper has
  * no counterpart; this entry point exists for callers that must not call
  * cudaMalloc at call time: code whose device memory is owned by another

@@ -103,6 +103,7 @@ def load():
                                      P(SolveOpts), P(SolveReport), _c_vp]
     lib.rbf_morton_order_noalloc.argtypes = [_c_vp, _c_i64, _c_int, _c_vp, _c_dbl, _c_int, _c_vp,
                                              _c_vp, _c_vp]
+    lib.rbf_peak_probe.argtypes = [_c_int, _c_dbl, P(_c_dbl), _c_vp]
     lib.rbf_knn.argtypes = [_c_vp, _c_vp, _c_vp]
     lib.rbf_cardinal_weights.argtypes = [_c_vp, _c_int, _c_dbl, _c_dbl, _c_vp, _c_i64, _c_vp, _c_vp]
     lib.rbf_precond_features.argtypes = [_c_vp, _c_dbl, _c_vp, _c_i64, _c_vp, _c_vp]
@@ -446,6 +447,18 @@ def interp_solve(tree: Tree, kernel: int, eps: float, u, lam, restart_m=50, max_
     if code not in (0, -4):
         raise RbfError(code, "rbf_interp_solve")
     return report
+
+
+PROBE_FFMA, PROBE_DFMA, PROBE_EX2, PROBE_RSQRT = 0, 1, 2, 3
+
+
+def peak_probe(kind, seconds=0.3):
+    """rbf_peak_probe: measured rate of one arithmetic unit (flop/s for the FMA kinds,
+    results/s for the multi-function unit kinds) on the current device."""
+    rate = _c_dbl(0.0)
+    _check(load().rbf_peak_probe(int(kind), float(seconds), ctypes.byref(rate), _stream()),
+           "rbf_peak_probe")
+    return rate.value
 
 
 def morton_order_noalloc(X, lo, side, depth, perm, keys):

@@ -50,6 +50,10 @@ def test_argument_errors_need_no_device(lib):
     assert lib.rbf_tree_build(None, 10, 2, None, 1.0, 2, None, ctypes.byref(out)) == -1
     assert lib.rbf_fmm_matvec(None, 0, 1.0, None, 0, None, 0, None, 0, 1, None) == -1
     assert lib.rbf_tree_get_info(None, None) == -1
+    rate = ctypes.c_double(0.0)
+    assert lib.rbf_peak_probe(0, ctypes.c_double(0.1), None, None) == -1       # no output
+    assert lib.rbf_peak_probe(0, ctypes.c_double(0.0), ctypes.byref(rate), None) == -1
+    assert lib.rbf_peak_probe(9, ctypes.c_double(0.1), ctypes.byref(rate), None) == -1  # kind
 
 
 def test_header_is_plain_c_and_links(lib, tmp_path):

@@ -43,7 +43,7 @@ def test_clock_summary_flags_thermal_and_missing_samples(tmp_path):
 
 
 def test_fp32_peak_from_unit_counts():
-    assert bench.fp32_peak_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert bench.fp32_peak_tflops(2070.0, 152) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
 
 
 def test_traffic_is_voided_when_the_source_changes(tmp_path, monkeypatch):
