@@ -3,21 +3,27 @@
 With RBF_FP32 and at least four columns, rbf_fmm_matvec runs P2M and L2P of
 several columns as complex matrix products on the tensor cores (three-term
 split TF32 operands, FP32 accumulation).  Every column must match the FP64
-oracle FMM to the FP32 bound of the single-column tests (5e-6 relative L2) and
-the single-column FP32 product to the same bound.  The cases cover several row
-and column tiles, several point tiles per leaf (leaves above 128 points),
-d = 1, 2, 3, 5, ragged clustered leaves, and more columns than one group holds.
+oracle FMM, and the single-column FP32 product, to the FP32 bound of the
+single-column tests in relative L2 (5e-6).  Element by element the bound is
+1.5e-5 of max |u_ref|: the split x = hi + lo with hi, lo in TF32 keeps about
+22 significant bits (2^-21 per product against 2^-24 for FP32 arithmetic), and
+the tensor core's accumulation rounds towards zero over each 12-MMA block, so
+the worst element of this path carries about 20x the error of the CUDA-core
+path (measured 6e-6 against 3e-7).  The cases cover several row and column
+tiles, several point tiles per leaf (leaves above 128 points), d = 1, 2, 3, 5,
+ragged clustered leaves, and more columns than one group holds.
 """
 import numpy as np
 import pytest
 
 import oracle as O
 import workloads
-from _parity import rel
+from _parity import errs
 
 pytestmark = pytest.mark.gpu
 
-FP32_TOL = 5e-6
+FP32_TOL = 5e-6        # relative L2
+TC_MAX_TOL = 1.5e-5    # element-wise, relative to max |u_ref| (tensor-core operand split)
 
 
 @pytest.fixture(scope="module")
@@ -82,14 +88,24 @@ def test_multi_rhs_matches_oracle_and_single_column(rbf, name, d, n, D, kernel, 
     rbf.check_device_waits()
     U = U.cpu().numpy()
     Us = Us.cpu().numpy()
-    worst_o = worst_s = 0.0
+    worst_o, worst_s = np.zeros(2), np.zeros(2)
+    occ = np.diff(T["leaf_off"])
+    where = None
     for c in range(R):
         ref = O.fmm(T, lam[c], kernel, eps, wc, M, L)
-        worst_o = max(worst_o, rel(U[c], ref))
-        worst_s = max(worst_s, rel(U[c], Us[c]))
-    print(f"{name}: R={R} max rel vs oracle {worst_o:.3e}, vs single-column FP32 {worst_s:.3e}")
-    assert worst_o <= FP32_TOL
-    assert worst_s <= FP32_TOL
+        eo = np.array(errs(U[c], ref))
+        if eo[1] > worst_o[1]:
+            i = int(np.argmax(np.abs(U[c] - ref)))
+            pos = int(np.flatnonzero(T["perm"] == i)[0])
+            leaf = int(np.searchsorted(T["leaf_off"], pos, side="right") - 1)
+            where = (c, leaf, int(occ[leaf]))
+        worst_o = np.maximum(worst_o, eo)
+        worst_s = np.maximum(worst_s, errs(U[c], Us[c]))
+    print(f"{name}: R={R} vs oracle rel-L2 {worst_o[0]:.2e} max {worst_o[1]:.2e} "
+          f"(column, leaf, leaf size {where}); vs single-column FP32 rel-L2 {worst_s[0]:.2e} "
+          f"max {worst_s[1]:.2e}")
+    assert worst_o[0] <= FP32_TOL and worst_o[1] <= TC_MAX_TOL
+    assert worst_s[0] <= FP32_TOL and worst_s[1] <= TC_MAX_TOL
 
 
 def test_multi_rhs_repeatable_and_leading_columns_independent(rbf):
@@ -136,14 +152,15 @@ def test_multi_rhs_5d_tensor_core_sampled(rbf):
     rbf.check_device_waits()
     U = U.cpu().numpy()
     Us = Us.cpu().numpy()
-    worst_s = max(rel(U[c], Us[c]) for c in range(R))
+    worst_s = np.max([errs(U[c], Us[c]) for c in range(R)], axis=0)
     T = O.tree(X, np.zeros(5), 1.0, 2)
     wc = O.coeffs_sampled(O.GAUSSIAN, eps, 5, M, L, 0.0, 1.0)
-    sample = np.random.default_rng(57).choice(len(X), size=16, replace=False)
-    worst_o = 0.0
+    sample = np.random.default_rng(57).choice(len(X), size=64, replace=False)
+    worst_o = np.zeros(2)
     for c in (0, 5, 10, 15):
         ref = O.fmm_at_targets(T, lam[c], O.GAUSSIAN, eps, wc, M, L, sample)
-        worst_o = max(worst_o, rel(U[c][sample], ref))
-    print(f"5d N=2^17 R=16: max rel vs oracle (sampled) {worst_o:.3e}, vs single-column {worst_s:.3e}")
-    assert worst_o <= FP32_TOL
-    assert worst_s <= FP32_TOL
+        worst_o = np.maximum(worst_o, errs(U[c][sample], ref))
+    print(f"5d N=2^17 R=16: vs oracle (sampled) rel-L2 {worst_o[0]:.2e} max {worst_o[1]:.2e}; "
+          f"vs single-column rel-L2 {worst_s[0]:.2e} max {worst_s[1]:.2e}")
+    assert worst_o[0] <= FP32_TOL and worst_o[1] <= TC_MAX_TOL
+    assert worst_s[0] <= FP32_TOL and worst_s[1] <= TC_MAX_TOL
