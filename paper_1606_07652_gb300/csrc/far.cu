@@ -471,6 +471,205 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? far_bmax(DENSE, NCE) : 256,
     }
 }
 
+// ------------------------------------------------------ L2P, FP32 Horner ---
+// Along the column dimension (d-1; dimension 0 when d == 1) the phases of a
+// point are powers of one unit-modulus number,
+//     e^{i xi_c r} = z^(c - coff),  z = e^{i dxi r},  coff = M/2 (0 when d == 1),
+// so the column sum of one mode row,  sum_c L[row][c] e^{i xi_c r},  is a
+// polynomial in z.  The NCOL = 8 q + r columns are cut into q groups of 8 (the
+// last one takes the r extra columns; a single group of r when q = 0).  Inside
+// a group the sum is taken by Horner's rule (degree <= 14, so the rounding of z
+// enters at most that often; with groups of 8 the FP32 error is that of the
+// direct sum), and each group value is multiplied by the exact phase of the
+// group's first column, e^{i xi_c0 r}, from the point's table.  The
+// multiply-adds per mode are those of the direct sum (one complex multiply-
+// add, 4 FP32 FMA), but the inner loop reads no shared memory: per point a
+// thread loads z, its groups' phases and its row factor.
+// A thread holds one whole mode row (NCOL <= 33 columns) in registers, loaded
+// straight from global memory, and walks the leaf's points two at a time; the
+// per-point sums of a warp are added by one transposed shuffle butterfly per
+// four points and kept per warp.
+constexpr int kHorner = 8;       // columns per Horner group (the last takes up to 7 more)
+constexpr int kHornerMaxCol = 33;
+constexpr int kHornerBlock = 192;  // 96 registers: three CTAs of six warps per SM
+constexpr int kHornerPch = 64;     // points per table chunk
+
+__device__ __forceinline__ float2 horner_step(float2 h, float2 z, float2 l)
+{
+    float2 r;
+    r.x = fmaf(h.x, z.x, l.x);
+    r.x = fmaf(-h.y, z.y, r.x);
+    r.y = fmaf(h.x, z.y, l.y);
+    r.y = fmaf(h.y, z.x, r.y);
+    return r;
+}
+
+// S_k (+)= ph_k * sum_{q<LEN} L[B+q] z_k^q for two points k
+template <int NC, int LEN, int B, bool FIRST>
+__device__ __forceinline__ void horner_group2(const float2 (&L)[NC], const float2 (&z)[2],
+                                              const float2 (&ph)[2], float2 (&S)[2])
+{
+    float2 h[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) h[k] = L[B + LEN - 1];
+#pragma unroll
+    for (int q = LEN - 2; q >= 0; --q)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) h[k] = horner_step(h[k], z[k], L[B + q]);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (FIRST) S[k] = cmul(ph[k], h[k]);
+        else cmac(S[k], ph[k], h[k]);
+    }
+}
+
+// all groups of a row; group g starts at column 8 g, its phase is rec[1 + g]
+template <int NC, int G>
+__device__ __forceinline__ void horner_groups(const float2 (&L)[NC], const float2 *ra,
+                                              const float2 *rb, const float2 (&z)[2],
+                                              float2 (&S)[2])
+{
+    constexpr int NG = NC >= kHorner ? NC / kHorner : 1;
+    constexpr int LEN = NC < kHorner ? NC : (G + 1 < NG ? kHorner : NC - kHorner * G);
+    if constexpr (G < NG) {
+        const float2 ph[2] = {ra[1 + G], rb[1 + G]};
+        horner_group2<NC, LEN, kHorner * G, G == 0>(L, z, ph, S);
+        horner_groups<NC, G + 1>(L, ra, rb, z, S);
+    }
+}
+
+// Re(A S) for the row factor A of one point (d == 3 specialised)
+template <bool D3>
+__device__ __forceinline__ float row_part(const float2 *Ep, int d, const RowOff &ro,
+                                          const float2 S)
+{
+    float2 A;
+    if (D3) A = cmul(Ep[ro.o0], Ep[ro.o1]);
+    else A = row_factor(Ep, d, ro);
+    return A.x * S.x - A.y * S.y;
+}
+
+template <int NC, bool D3>
+__device__ __forceinline__ void horner_rows(const FarArgs<float> &a, const float2 *E, int rowlen,
+                                            int rflen, int cnt, float *part)
+{
+    using C = float2;
+    const int d = a.d, nrow = a.nrow;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool hi16 = lane >= 16, hi8 = (lane & 8) != 0;
+    const C *Lleaf = a.Lx + (int64_t)blockIdx.x * a.mstride;
+    float *wpart = part + warp * a.pch;
+    for (int row0 = 0; row0 < nrow; row0 += blockDim.x) {
+        if (row0 + warp * 32 >= nrow) break;  // the whole warp is past the last row
+        const int row = row0 + threadIdx.x;
+        const bool act = row < nrow;
+        C L[NC];
+        const C *lrow = Lleaf + (int64_t)(act ? row : 0) * a.ncol;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            if (act && q < a.ncol) L[q] = lrow[q];
+            else L[q].x = L[q].y = 0.f;
+        }
+        const RowOff ro = row_offsets(act ? row : 0, d, a.n1, a.seg0, a.seg);
+        for (int p = 0; p < cnt; p += 4) {
+            float v[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int pa = min(p + 2 * h, cnt - 1), pb = min(p + 2 * h + 1, cnt - 1);
+                const C *Ea = E + pa * rowlen, *Eb = E + pb * rowlen;
+                const C z[2] = {Ea[rflen], Eb[rflen]};
+                C S[2];
+                horner_groups<NC, 0>(L, Ea + rflen, Eb + rflen, z, S);
+                const float va = row_part<D3>(Ea, d, ro, S[0]);
+                const float vb = row_part<D3>(Eb, d, ro, S[1]);
+                v[2 * h] = act && p + 2 * h < cnt ? va : 0.f;
+                v[2 * h + 1] = act && p + 2 * h + 1 < cnt ? vb : 0.f;
+            }
+            // warp sums of the four points: lanes < 16 keep points 0, 1 and lanes >= 16
+            // points 2, 3; (lane & 8) then picks one of the pair; a butterfly over the
+            // remaining 8 lanes
+            const float k0 = (hi16 ? v[2] : v[0]) + __shfl_xor_sync(0xffffffffu, hi16 ? v[0] : v[2], 16);
+            const float k1 = (hi16 ? v[3] : v[1]) + __shfl_xor_sync(0xffffffffu, hi16 ? v[1] : v[3], 16);
+            float w = (hi8 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            if ((lane & 7) == 0) {
+                const int pk = p + (hi16 ? 2 : 0) + (hi8 ? 1 : 0);
+                if (pk < cnt) wpart[pk] += w;
+            }
+        }
+    }
+}
+
+template <int NC>
+__global__ void __maxnreg__(96) k_l2p_horner(FarArgs<float> a, int reclen)
+{
+    using C = float2;
+    constexpr int NG = NC >= kHorner ? NC / kHorner : 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int d = a.d, seg0 = a.seg0, seg = a.seg;
+    const int rflen = d == 1 ? 0 : seg0 + (d - 2) * seg;  // row-factor tables (dims 0..d-2)
+    const int rowlen = rflen + reclen;
+    const int nwarp = blockDim.x >> 5;
+    C *E = reinterpret_cast<C *>(smem_raw);                                // [pch][rowlen]
+    float *part = reinterpret_cast<float *>(E + (size_t)a.pch * rowlen);   // [nwarp][pch]
+    const int leaf = blockIdx.x;
+    const int64_t p0 = a.leaf_off[leaf];
+    const int np = a.leaf_off[leaf + 1] - (int)p0;
+    double c[RBF_MAX_DIM];
+    leaf_centre(a.leaf_key[leaf], d, a.D, a.lo, a.side, c);
+    const int cdim = d - 1;
+    const int xoff = d == 1 ? a.M / 2 : 0;  // xi index of column q is q + xoff
+    for (int ch0 = 0; ch0 < np; ch0 += a.pch) {
+        const int cnt = min(a.pch, np - ch0);
+        __syncthreads();
+        // per point: the row-factor tables, then z and the first-column phase of
+        // every group
+        for (int idx = threadIdx.x; idx < cnt * rowlen; idx += blockDim.x) {
+            const int p = idx / rowlen, j = idx - p * rowlen;
+            int t, kidx;
+            bool pad;
+            if (j < rflen) {
+                if (j < seg0) {
+                    t = 0;
+                    kidx = j + a.M / 2;
+                    pad = j >= a.n0;
+                } else {
+                    t = 1 + (j - seg0) / seg;
+                    kidx = (j - seg0) % seg;
+                    pad = kidx >= a.n1;
+                }
+            } else {
+                const int q = j - rflen;
+                t = cdim;
+                pad = q > NG;
+                kidx = q == 0 ? a.M / 2 + 1 : kHorner * (q - 1) + xoff;
+            }
+            C e;
+            if (pad) {
+                e.x = e.y = 0.f;
+            } else {
+                const float r = a.xs[(int64_t)t * a.N + p0 + ch0 + p] - (float)c[t];
+                float sn, co;
+                sincos_r(a.xi[kidx] * r, &sn, &co);
+                e.x = co;
+                e.y = sn;
+            }
+            E[idx] = e;
+        }
+        for (int q = threadIdx.x; q < nwarp * a.pch; q += blockDim.x) part[q] = 0.f;
+        __syncthreads();
+        if (d == 3) horner_rows<NC, true>(a, E, rowlen, rflen, cnt, part);
+        else horner_rows<NC, false>(a, E, rowlen, rflen, cnt, part);
+        __syncthreads();
+        for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+            float sum = 0.f;
+            for (int w = 0; w < nwarp; ++w) sum += part[w * a.pch + p];
+            a.u[p0 + ch0 + p] = sum;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ M2M ---
 // M2M for d <= 3, two consecutive modes per thread: every child value of the
 // pair is loaded (one 16-byte load in FP32) before any arithmetic, so the
@@ -1167,7 +1366,55 @@ int rbf_run_p2m(rbf_tree *t, const rbf_plan *p, const R *lam_s, cplx<R> *V, cuda
     return dispatch_p2m_l2p<R>(false, a, t->nleaf(), s);
 }
 
-// L2P of one column from the leaf local expansions L
+namespace {
+template <int NC>
+int launch_l2p_horner(const FarArgs<float> &a0, int nleaf, cudaStream_t s)
+{
+    constexpr int NG = NC >= kHorner ? NC / kHorner : 1;
+    FarArgs<float> a = a0;
+    a.seg0 = a.d == 1 ? 0 : even_up(a.n0);
+    a.seg = even_up(a.n1);
+    const int reclen = even_up(NG + 1);
+    const int rflen = a.d == 1 ? 0 : a.seg0 + (a.d - 2) * a.seg;
+    const int rowlen = rflen + reclen;
+    const int bd = std::min(kHornerBlock, 32 * ((a.nrow + 31) / 32));
+    a.pch = kHornerPch;
+    const size_t smem = (size_t)a.pch * (rowlen * sizeof(float2) + (bd / 32) * sizeof(float));
+    RBF_CUDA_TRY(cudaFuncSetAttribute(k_l2p_horner<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    k_l2p_horner<NC><<<nleaf, bd, smem, s>>>(a, reclen);
+    RBF_LAUNCH_CHECK();
+    return RBF_OK;
+}
+
+// rows of up to 33 columns; an even count runs with one zero column more
+int l2p_horner(const FarArgs<float> &a, int nleaf, cudaStream_t s)
+{
+    switch ((a.ncol + 1) / 2) {
+        case 1: return launch_l2p_horner<3>(a, nleaf, s);
+        case 2: return launch_l2p_horner<3>(a, nleaf, s);
+        case 3: return launch_l2p_horner<5>(a, nleaf, s);
+        case 4: return launch_l2p_horner<7>(a, nleaf, s);
+        case 5: return launch_l2p_horner<9>(a, nleaf, s);
+        case 6: return launch_l2p_horner<11>(a, nleaf, s);
+        case 7: return launch_l2p_horner<13>(a, nleaf, s);
+        case 8: return launch_l2p_horner<15>(a, nleaf, s);
+        case 9: return launch_l2p_horner<17>(a, nleaf, s);
+        case 10: return launch_l2p_horner<19>(a, nleaf, s);
+        case 11: return launch_l2p_horner<21>(a, nleaf, s);
+        case 12: return launch_l2p_horner<23>(a, nleaf, s);
+        case 13: return launch_l2p_horner<25>(a, nleaf, s);
+        case 14: return launch_l2p_horner<27>(a, nleaf, s);
+        case 15: return launch_l2p_horner<29>(a, nleaf, s);
+        case 16: return launch_l2p_horner<31>(a, nleaf, s);
+        default: return launch_l2p_horner<33>(a, nleaf, s);
+    }
+}
+}  // namespace
+
+// L2P of one column from the leaf local expansions L: FP32 rows of up to
+// kHornerMaxCol columns by the Horner kernel; wider rows and FP64 by the table
+// kernel.
 template <typename R>
 int rbf_run_l2p(rbf_tree *t, const rbf_plan *p, const cplx<R> *L, R *u_far, cudaStream_t s)
 {
@@ -1175,6 +1422,9 @@ int rbf_run_l2p(rbf_tree *t, const rbf_plan *p, const cplx<R> *L, R *u_far, cuda
     a.Lx = L;
     a.u = u_far;
     rbf_pass_timer tm(t, RBF_PASS_L2P, s);
+    if constexpr (sizeof(R) == 4) {
+        if (a.ncol <= kHornerMaxCol) return l2p_horner(a, t->nleaf(), s);
+    }
     return dispatch_p2m_l2p<R>(true, a, t->nleaf(), s);
 }
 
