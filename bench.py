@@ -321,7 +321,7 @@ def run_ours(args):
         if args.batch:
             out["batch"] = batch_measurement(rbf, dev)
         if args.solve:
-            out["solve"] = solve_measurement(rbf, dev)
+            out["solve"] = solve_measurement(rbf, dev, big=args.solve > 1 or args.solve_big)
         if args.mrhs:
             out["multi_rhs"] = multi_rhs_measurement(rbf, dev, nrhs=args.mrhs_cols, n=args.mrhs_n,
                                                      M=args.mrhs_M)
@@ -551,47 +551,144 @@ def batch_measurement(rbf, dev, n_problems=256, steps=5):
             "depth_range": [int(lay["depth"].min()), int(lay["depth"].max())]}
 
 
-def solve_measurement(rbf, dev):
-    """Clustered 3-D Gaussian workload (N = 262,144, eps = 3): plain FP64 FMM-GMRES with a
-    150-iteration budget, then FP32 products + FP64 refinement (plain, and with the learned
-    preconditioner and its fallback) asked to reach the residual the FP64 solve reached.
-    The FP64 residual floor of this flat system is far above 1e-8 (design notes), so the
-    comparison is time to a common reachable residual."""
+def _curve(hist, every=5):
+    """Residual history as compact [iterations, seconds, residual] rows: every FP64
+    true residual and every `every`-th inner restart residual."""
+    out, k = [], 0
+    for it, sec, r, kind in hist:
+        if kind == 0 or k % every == 0:
+            out.append([it, round(sec, 4), r, "fp64" if kind == 0 else "inner"])
+        if kind == 1:
+            k += 1
+    return out
+
+
+def _time_to(hist, target, inner_true=False):
+    """Seconds at which the true residual first reached target (None if never); with an
+    FP64 inner product the restart residuals of a cold start are true residuals too."""
+    for it, sec, r, kind in hist:
+        if (kind == 0 or inner_true) and r <= target:
+            return sec
+    return None
+
+
+def _floor(hist, inner_true=False):
+    return min(r for it, sec, r, kind in hist if kind == 0 or inner_true)
+
+
+def solve_leg(rbf, dev, n, depth, fp64_iters, fp32_iters):
+    """The clustered 3-D Gaussian workload (8 Gaussians, sd 0.05, eps = 3, M = 24, L = 3) at n
+    centres: plain FP64 FMM-GMRES(50) for at most fp64_iters iterations, FP32 products with
+    FP64 refinement, and FP32 with the learned preconditioner (trained on 16,384 of the
+    centres, judged by its trial cycle), all asked for 1e-8; residual against wall time for
+    each, the floor each reaches and the time each takes to the common reachable residual."""
     import torch
     import workloads
     from paper_1606_07652_gb300 import _lib
-    X, u, p = workloads.config3()
+    X, u, p = workloads.config3(n)
     Xd = torch.as_tensor(X, device=dev)
     ud = torch.as_tensor(u, device=dev)
-    t = rbf.tree_build(Xd, lo=np.zeros(3), side=1.0, depth=6)
-    kw = dict(M=p["M"], period_L=p["L"], window_alpha=p["alpha"])
-    res = {"workload": "3D N=262144 clustered (8 Gaussians, sd 0.05), Gaussian eps=3, depth 6, "
-                       "M=24, L=3"}
-    # plain FP64 FMM-GMRES(50) with a budget of 150 iterations
+    t = rbf.tree_build(Xd, lo=np.zeros(3), side=1.0, depth=depth)
+    kw = dict(M=p["M"], period_L=p["L"], window_alpha=p["alpha"], history=4096)
+    res = {"workload": "3D N=%d clustered (8 Gaussians, sd 0.05), Gaussian eps=3, depth %d, M=24, "
+                       "L=3, u = sin(2 pi x) cos(2 pi y) exp(-z), target 1e-8" % (len(X), depth)}
     lam = torch.zeros_like(ud)
-    r64 = rbf.interp_solve(t, p["kernel"], p["eps"], ud, lam, restart_m=50, max_iters=150,
-                           max_refine=2, rtol=1e-8, inner_prec=rbf.FP64, precond=0, **kw)
-    res["fp64_plain"] = r64
-    # FP32 products + FP64 refinement: time to reach the residual the FP64 solve reached
-    target = max(r64["rel_resid"], 1e-8)
-    res["target_rel_resid"] = target
+    r64 = rbf.interp_solve(t, p["kernel"], p["eps"], ud, lam, restart_m=50, max_iters=fp64_iters,
+                           max_refine=1, rtol=1e-8, inner_prec=rbf.FP64, precond=0, **kw)
     lam.zero_()
-    res["fp32_refined_plain"] = rbf.interp_solve(
-        t, p["kernel"], p["eps"], ud, lam, restart_m=50, max_iters=3000, max_refine=6, rtol=target,
-        inner_prec=rbf.FP32, precond=0, **kw)
+    r32 = rbf.interp_solve(t, p["kernel"], p["eps"], ud, lam, restart_m=50, max_iters=fp32_iters,
+                           max_refine=8, rtol=1e-8, inner_prec=rbf.FP32, precond=0, **kw)
     net = _lib.Mlp(96, 128, 32, seed=3)
-    res["train"] = _lib.precond_train(t, p["kernel"], p["eps"], net, n_train=16384, epochs=40,
-                                      batch=1024, lr=1e-3, delta_rel=1e-12)
+    train = _lib.precond_train(t, p["kernel"], p["eps"], net, n_train=16384, epochs=40,
+                               batch=1024, lr=1e-3, delta_rel=1e-12)
     t0 = time.perf_counter()
     _lib.precond_build(t, p["kernel"], p["eps"], net)
-    res["precond_build_s"] = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
     lam.zero_()
-    res["fp32_refined_learned"] = rbf.interp_solve(
-        t, p["kernel"], p["eps"], ud, lam, restart_m=50, max_iters=3000, max_refine=6, rtol=target,
-        inner_prec=rbf.FP32, precond=1, **kw)
+    rl = rbf.interp_solve(t, p["kernel"], p["eps"], ud, lam, restart_m=50, max_iters=fp32_iters,
+                          max_refine=8, rtol=1e-8, inner_prec=rbf.FP32, precond=1, **kw)
     t.free()
     net.free()
+    legs = (("fp64_plain", r64, True), ("fp32_refined_plain", r32, False),
+            ("fp32_refined_learned", rl, False))
+    common = max(_floor(r["history"], tr) for _, r, tr in legs)
+    for name, r, tr in legs:
+        hist = r.pop("history")
+        r["floor"] = _floor(hist, tr)
+        r["seconds_to_common"] = _time_to(hist, common, tr)
+        r["curve"] = _curve(hist, every=1 if len(hist) < 40 else 5)
+        res[name] = r
+    t64, t32 = res["fp64_plain"]["seconds_to_common"], res["fp32_refined_plain"]["seconds_to_common"]
+    tl = res["fp32_refined_learned"]["seconds_to_common"]
+    res["speedup_to_common"] = {"fp32_refined_plain": t64 / t32 if t64 and t32 else None,
+                                "fp32_refined_learned": t64 / tl if t64 and tl else None}
+    res["train"] = train
+    res["precond_build_s"] = build_s
+    res["common_rel_resid"] = common
+    res["target_1e-8_reached"] = {k: res[k]["floor"] <= 1e-8
+                                  for k in ("fp64_plain", "fp32_refined_plain",
+                                            "fp32_refined_learned")}
+    res["fp64_iteration_cap"] = fp64_iters
     return res
+
+
+def learned_gain_leg(rbf, dev, n=1 << 18, eh=1.2):
+    """A regime where local cardinal functions are local: 3-D, n centres uniform in the
+    unit cube (spacing h = n^(-1/3)), Gaussian eps = eh / h.  The autotuner picks no far
+    field (the kernel is below 1e-10 beyond one leaf).  FP32 products with FP64
+    refinement to 1e-8: plain, learned P (network trained at this eps*h on 16,384 of the
+    centres) and exact local cardinal P."""
+    import torch
+    import workloads
+    from paper_1606_07652_gb300 import _lib
+    X, _ = workloads.uniform(n, 3, 12)
+    u = np.sin(2 * np.pi * X[:, 0]) * np.cos(2 * np.pi * X[:, 1]) * np.exp(-X[:, 2])
+    eps = eh * round(n ** (1.0 / 3.0))
+    prm = _lib.autotune(rbf.GAUSSIAN, eps, 3, n, 1e-10)
+    Xd = torch.as_tensor(X, device=dev)
+    ud = torch.as_tensor(u, device=dev)
+    t = rbf.tree_build(Xd, lo=np.zeros(3), side=1.0, depth=prm["depth"])
+    kw = dict(M=prm["M"], period_L=prm["period_L"], window_alpha=prm["window_alpha"],
+              restart_m=50, max_iters=3000, max_refine=10, rtol=1e-8, inner_prec=rbf.FP32)
+    res = {"workload": "3D N=%d uniform, Gaussian eps=%.1f (eps*h=%.1f), autotuned depth %d, "
+                       "M=%d (far-kernel error %.1e)" % (n, eps, eh, prm["depth"], prm["M"],
+                                                         prm["err"])}
+    lam = torch.zeros_like(ud)
+    res["plain"] = rbf.interp_solve(t, rbf.GAUSSIAN, eps, ud, lam, precond=0, **kw)
+    net = _lib.Mlp(96, 128, 32, seed=3)
+    res["train"] = _lib.precond_train(t, rbf.GAUSSIAN, eps, net, n_train=16384, epochs=400,
+                                      batch=1024, lr=1e-3, delta_rel=1e-12)
+    t0 = time.perf_counter()
+    _lib.precond_build(t, rbf.GAUSSIAN, eps, net)
+    torch.cuda.synchronize()
+    res["learned_build_s"] = time.perf_counter() - t0
+    lam.zero_()
+    res["learned"] = rbf.interp_solve(t, rbf.GAUSSIAN, eps, ud, lam, precond=1, **kw)
+    t0 = time.perf_counter()
+    _lib.precond_build(t, rbf.GAUSSIAN, eps, None)
+    torch.cuda.synchronize()
+    res["exact_build_s"] = time.perf_counter() - t0
+    lam.zero_()
+    res["exact_local"] = rbf.interp_solve(t, rbf.GAUSSIAN, eps, ud, lam, precond=1, **kw)
+    t.free()
+    net.free()
+    pl, le = res["plain"], res["learned"]
+    res["learned_vs_plain"] = {"iters": [le["iters"], pl["iters"]],
+                               "seconds": [le["seconds"], pl["seconds"]],
+                               "fewer_iterations": le["iters"] < pl["iters"],
+                               "less_time": le["seconds"] < pl["seconds"]}
+    return res
+
+
+def solve_measurement(rbf, dev, big=True):
+    """The solve half of the metric: the clustered workload at N = 262,144 and at
+    N = 2^20 (FP64 capped to bound the run), and the learned-preconditioner leg."""
+    out = {"n262144": solve_leg(rbf, dev, 262144, 6, fp64_iters=150, fp32_iters=1500)}
+    if big:
+        out["n1048576"] = solve_leg(rbf, dev, 1 << 20, 7, fp64_iters=60, fp32_iters=600)
+    out["learned_gain"] = learned_gain_leg(rbf, dev)
+    return out
 
 
 def multi_rhs_measurement(rbf, dev, tol=1.5e-7, nrhs=16, n=1 << 19, M=0):
@@ -742,6 +839,8 @@ def main():
     ap.add_argument("--kernels", type=int, default=1,
                     help="also run the IMQ / MQ / Wendland error-vs-M sweep")
     ap.add_argument("--solve", type=int, default=1, help="also run the solve comparison")
+    ap.add_argument("--solve-big", type=int, default=1,
+                    help="include the N=2^20 solve leg (about a minute)")
     ap.add_argument("--mrhs", type=int, default=1,
                     help="also time the 5D 16-column product on the tensor cores")
     ap.add_argument("--mrhs-n", type=int, default=1 << 19, help="centres of the 5D product")

@@ -67,7 +67,12 @@ typedef enum { RBF_FP64 = 0, RBF_FP32 = 1 } rbf_precision;
 /* Parameters of the band-limited expansion (Sec. 3.2, "Low-rank representation").
  *  M            quadrature nodes per dimension (even, 2..64).  The nodes are
  *               xi_k = k * 2pi/L, k = -M/2..M/2, with half weight at +-M/2,
- *               so the band limit is sigma = pi M / L.
+ *               so the band limit is sigma = pi M / L.  M = 0: no far field;
+ *               the product is the near field alone (far kernel K = 0), which
+ *               is within max_far |Phi| (rbf_kernel_error) of the exact product:
+ *               for kernels that vanish beyond one leaf width (narrow
+ *               Gaussians, compact supports).  The other fields are then
+ *               ignored except grid, which must be RBF_GRID_SHARED.
  *  period_L     period of the sampled kernel; must exceed the root side (twice
  *               the root side when window_alpha > 0).  Far offsets have
  *               components below `side`, so Phi(L - side) bounds the image error.
@@ -211,7 +216,18 @@ RBF_API int rbf_direct_sum(const double *X, int64_t N, int d, rbf_kernel kernel,
  *  inner_prec  arithmetic of the matvec inside GMRES (RBF_FP64 or RBF_FP32).
  *  precond     0: none (the diagonal of A is Phi(0) = 1, so the diagonal
  *              preconditioner is the identity); 1: learned sparse approximate
- *              inverse (built with rbf_precond_build). */
+ *              inverse (built with rbf_precond_build).  With precond = 1 the
+ *              first correction step is a trial: one GMRES cycle of restart_m
+ *              iterations with P; if its inner solve does not converge within
+ *              that cycle, one plain cycle from the same iterate follows and
+ *              the iterate with the smaller FP64 residual is kept (P is
+ *              dropped, used_fallback = 1, when the plain cycle wins).  A P
+ *              that does not help therefore costs at most one cycle.  Later
+ *              steps also drop P when a preconditioned step fails to halve
+ *              the FP64 residual.
+ *  history_host  optional (NULL: none): host array of 4 * history_cap
+ *              doubles that receives the residual history (rbf_solve_report).
+ *  history_cap   its capacity in entries. */
 typedef struct {
     int restart_m;
     int max_iters;
@@ -219,17 +235,28 @@ typedef struct {
     double rtol;
     rbf_precision inner_prec;
     int precond;
+    double *history_host;
+    int history_cap;
 } rbf_solve_opts;
 
-/* Per-solve report (host struct). */
+/* Per-solve report (host struct).  When rbf_solve_opts::history_host is set,
+ * the solve appends one entry (inner iterations so far, seconds since the
+ * start, relative residual, kind) at every FP64 true residual (kind
+ * RBF_HIST_FP64: ||u - A64 lambda|| / ||u||) and at every GMRES restart
+ * (kind RBF_HIST_INNER: the residual of the inner correction equation, with
+ * the inner-precision product, over ||u||), stops at history_cap entries and
+ * reports the count in history_len. */
+#define RBF_HIST_FP64 0
+#define RBF_HIST_INNER 1
 typedef struct {
     int iters;            /* inner GMRES iterations, all restarts */
-    int refinements;      /* outer refinement steps taken */
+    int refinements;      /* correction steps taken (GMRES calls) */
     int used_fallback;    /* 1 when the learned preconditioner was dropped */
     double rel_resid;     /* final ||u - A64 lambda|| / ||u|| */
     double seconds;       /* wall time of the solve */
     int matvecs_inner;    /* products in inner arithmetic */
     int matvecs_fp64;     /* FP64 products for true residuals */
+    int history_len;      /* residual-history entries written */
 } rbf_solve_report;
 
 /* Solve A lambda = u (one right-hand side at a time, nrhs columns) with
@@ -422,8 +449,9 @@ RBF_API int rbf_kernel_error(rbf_kernel kernel, double eps, int d, const rbf_fmm
  * tol / 100; Wendland: no taper, L just above side + 1/eps so that the support
  * never wraps; inverse multiquadric and multiquadric: L = 4 side,
  * alpha = 4.5) and the smallest even M in [8, 64] whose measured far-kernel
- * error (rbf_kernel_error) is <= tol (64 when none is).  *err_out (may be
- * NULL) receives the achieved error. */
+ * error (rbf_kernel_error) is <= tol (64 when none is); M = 0 (no far field)
+ * when max |Phi| over the far offsets of that depth is already <= tol.
+ * *err_out (may be NULL) receives the achieved error. */
 RBF_API int rbf_autotune(rbf_kernel kernel, double eps, int d, int64_t N, double side, double tol,
                          rbf_fmm_params *params_out, int *depth_out, double *err_out);
 

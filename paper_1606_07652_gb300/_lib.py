@@ -42,13 +42,14 @@ class TreeInfo(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("restart_m", _c_int), ("max_iters", _c_int), ("max_refine", _c_int),
-                ("rtol", _c_dbl), ("inner_prec", _c_int), ("precond", _c_int)]
+                ("rtol", _c_dbl), ("inner_prec", _c_int), ("precond", _c_int),
+                ("history_host", ctypes.POINTER(_c_dbl)), ("history_cap", _c_int)]
 
 
 class SolveReport(ctypes.Structure):
     _fields_ = [("iters", _c_int), ("refinements", _c_int), ("used_fallback", _c_int),
                 ("rel_resid", _c_dbl), ("seconds", _c_dbl), ("matvecs_inner", _c_int),
-                ("matvecs_fp64", _c_int)]
+                ("matvecs_fp64", _c_int), ("history_len", _c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -429,12 +430,20 @@ def direct_sum(X, kernel: int, eps: float, lam, targets, u):
 
 def interp_solve(tree: Tree, kernel: int, eps: float, u, lam, restart_m=50, max_iters=2000,
                  max_refine=10, rtol=1e-8, inner_prec=FP32, precond=0, M=None, period_L=None,
-                 window_alpha=None, csample=1, grid=GRID_SHARED, lagrange_K=0):
-    """rbf_interp_solve: u, lam float64 CUDA tensors (N,) or (nrhs, N); lam holds the guess."""
+                 window_alpha=None, csample=1, grid=GRID_SHARED, lagrange_K=0, history=0):
+    """rbf_interp_solve: u, lam float64 CUDA tensors (N,) or (nrhs, N); lam holds the guess.
+    history > 0 returns up to that many residual-history entries under "history" as
+    (iterations, seconds, relative residual, kind) rows, kind 0 = FP64 true residual,
+    1 = inner restart residual."""
     info = tree.info()
     nrhs = _block(info["N"], u, lam, ("u", "lam"))
     o = SolveOpts(restart_m, max_iters, max_refine, rtol, inner_prec, precond)
     rep = SolveReport()
+    hist = None
+    if history > 0:
+        hist = (_c_dbl * (4 * int(history)))()
+        o.history_host = ctypes.cast(hist, ctypes.POINTER(_c_dbl))
+        o.history_cap = int(history)
     p = _params(M, period_L, window_alpha, csample, kernel, info["side"], grid, lagrange_K)
     code = load().rbf_interp_solve(tree.handle, kernel, float(eps),
                                    ctypes.byref(p) if p is not None else None,
@@ -444,6 +453,9 @@ def interp_solve(tree: Tree, kernel: int, eps: float, u, lam, restart_m=50, max_
               "used_fallback": rep.used_fallback, "rel_resid": rep.rel_resid,
               "seconds": rep.seconds, "matvecs_inner": rep.matvecs_inner,
               "matvecs_fp64": rep.matvecs_fp64}
+    if hist is not None:
+        h = np.frombuffer(hist, dtype=np.float64)[:4 * rep.history_len].reshape(-1, 4)
+        report["history"] = [[int(r[0]), float(r[1]), float(r[2]), int(r[3])] for r in h]
     if code not in (0, -4):
         raise RbfError(code, "rbf_interp_solve")
     return report

@@ -41,8 +41,11 @@ __global__ void k_kernel_error(int d, int M, int64_t nmode, const double *xi, co
         r[t] = (2.0 * ((h >> 11) * (1.0 / 9007199254740992.0)) - 1.0) * side;
         linf = fmax(linf, fabs(r[t]));
     }
-    // push the offset out of the near zone along its largest component
-    if (linf < w) {
+    // push the offset out of the near zone along its largest component; with no
+    // far field (M = 0, K = 0) the first sample is the nearest far offset itself
+    if (M == 0 && q == 0) {
+        for (int t = 0; t < d; ++t) r[t] = t == 0 ? w : 0.0;
+    } else if (linf < w) {
         int tm = 0;
         for (int t = 1; t < d; ++t)
             if (fabs(r[t]) > fabs(r[tm])) tm = t;
@@ -221,6 +224,19 @@ extern "C" int rbf_autotune(rbf_kernel kernel, double eps, int d, int64_t N, dou
         p.M = M;
         return rbf_kernel_error(kernel, eps, d, &p, side, D, e);
     };
+    // no far field at all when the kernel is within tol beyond one leaf width
+    // (K = 0 is then a far kernel within tol: narrow Gaussians, compact supports)
+    {
+        double e0 = INFINITY;
+        RBF_TRY(error_at(0, &e0));
+        if (e0 <= tol) {
+            p.M = 0;
+            *out = p;
+            *depth_out = D;
+            if (err_out) *err_out = e0;
+            return RBF_OK;
+        }
+    }
     const double lt = std::log(1.0 / tol);
     // (the Wendland function's transform decays only algebraically: start at 16)
     const double pred = kernel == RBF_GAUSSIAN ? 2.0 * eps * p.period_L * std::sqrt(lt) / M_PI

@@ -1076,7 +1076,7 @@ int launch_l2p(const TcArgs &a, const float2 *Eg, int rowpadE, int Rg, int nptil
 
 int rbf_far_multi_supported(const rbf_plan *p)
 {
-    return p->ncol <= kMaxNT && p->grid == RBF_GRID_SHARED;
+    return p->M > 0 && p->ncol <= kMaxNT && p->grid == RBF_GRID_SHARED;
 }
 
 int rbf_run_far_multi(rbf_tree *t, rbf_plan *p, const float *lam_s, int G, float2 *V, float2 *L,

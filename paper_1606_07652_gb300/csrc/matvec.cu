@@ -36,7 +36,7 @@ int matvec_one(rbf_tree *t, rbf_plan *p, int kernel, double eps, const double *l
         RBF_LAUNCH_CHECK();
     }
     RBF_TRY(rbf_run_p2p<R>(t, kernel, eps, lam_s, un, s));
-    const bool far = t->D >= 2;
+    const bool far = t->D >= 2 && p->M > 0;  // M = 0: near field alone
     if (far) RBF_TRY(rbf_run_far<R>(t, p, lam_s, uf, s));
     {
         rbf_pass_timer tm(t, RBF_PASS_PERM, s);
@@ -115,7 +115,7 @@ int matvec_multi(rbf_tree *t, rbf_plan *p, int kernel, double eps, const double 
     int G = 0;
     RBF_TRY(multi_workspace(t, p, R, &G));
     const int64_t N = t->N;
-    const bool far = t->D >= 2;
+    const bool far = t->D >= 2 && p->M > 0;  // M = 0: near field alone
     for (int c0 = 0; c0 < R; c0 += G) {
         const int g = std::min(G, R - c0);
         {

@@ -291,11 +291,14 @@ int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_param
     RBF_REQUIRE(kernel != RBF_MQ || pp->window_alpha > 0.0,
                 "the multiquadric grows with r: window_alpha must be > 0");
     RBF_REQUIRE(eps > 0.0 && std::isfinite(eps), "eps must be positive and finite");
-    RBF_REQUIRE(pp->M >= 2 && pp->M <= 64 && pp->M % 2 == 0, "M=%d must be even in [2, 64]", pp->M);
+    // M = 0: no far field (the product is the near field alone)
+    RBF_REQUIRE(pp->M == 0 || (pp->M >= 2 && pp->M <= 64 && pp->M % 2 == 0),
+                "M=%d must be 0 or even in [2, 64]", pp->M);
+    RBF_REQUIRE(pp->M > 0 || pp->grid == RBF_GRID_SHARED, "M = 0 (no far field) needs the shared grid");
     RBF_REQUIRE(pp->window_alpha >= 0.0, "window_alpha must be >= 0");
     // far offsets reach |r_t| < side: the nearest image sits at >= L - side, and
     // the taper needs a transition zone L - 2 side > 0
-    RBF_REQUIRE(pp->period_L > (pp->window_alpha > 0.0 ? 2.0 : 1.0) * t->side,
+    RBF_REQUIRE(pp->M == 0 || pp->period_L > (pp->window_alpha > 0.0 ? 2.0 : 1.0) * t->side,
                 "period_L=%g must exceed %s the root side %g", pp->period_L,
                 pp->window_alpha > 0.0 ? "twice" : "", t->side);
     RBF_REQUIRE(pp->csample == 0 || pp->csample == 1, "csample must be 0 or 1");
@@ -319,6 +322,7 @@ int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_param
     const int d = t->d, M = pp->M;
     int64_t nmode = M / 2 + 1;
     for (int q = 1; q < d; ++q) nmode *= (M + 1);
+    if (M == 0) nmode = 0;
     if (p && p->kernel == kernel && p->eps == eps && p->M == M && p->L == pp->period_L &&
         p->alpha == pp->window_alpha && p->csample == pp->csample && p->grid == pp->grid &&
         p->lagK == lagK) {
@@ -359,7 +363,9 @@ int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_param
         p->ncol = p->n1;
         p->nrow = (int)(nmode / p->n1);
     }
-    int st = prec == RBF_FP64 ? build_tables<double>(t, p, s) : build_tables<float>(t, p, s);
+    if (M == 0) p->n0 = p->n1 = p->nrow = p->ncol = 0;
+    int st = M == 0 ? RBF_OK
+                    : (prec == RBF_FP64 ? build_tables<double>(t, p, s) : build_tables<float>(t, p, s));
     if (st == RBF_OK && fresh) st = prec == RBF_FP64 ? alloc_work<double>(t, p) : alloc_work<float>(t, p);
     if (st == RBF_OK && p->grid == RBF_GRID_NESTED) st = rbf_nested_build(t, p, s);
     if (st != RBF_OK) {

@@ -118,6 +118,22 @@ struct Solver {
     std::vector<double> hh;  // host copy of reductions
     int mv_inner = 0, mv64 = 0;
     bool use_p = false;      // right preconditioner P attached to the tree
+    // residual history (rbf_solve_opts::history_host): iterations, seconds,
+    // relative residual, kind
+    double *hist = nullptr;
+    int hist_cap = 0, hist_len = 0;
+    int it_base = 0;         // inner iterations taken before the current GMRES call
+    double nu = 1.0;         // ||u|| of the column being solved
+    std::chrono::steady_clock::time_point t0;
+    void record(int iters, double rel, int kind)
+    {
+        if (!hist || hist_len >= hist_cap) return;
+        double *e = hist + 4 * (size_t)hist_len++;
+        e[0] = iters;
+        e[1] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        e[2] = rel;
+        e[3] = kind;
+    }
 
     int alloc(int m_)
     {
@@ -256,6 +272,7 @@ struct Solver {
             k_sub<<<gb, bs, 0, s>>>(b, w, r, n);
             RBF_LAUNCH_CHECK();
             RBF_TRY(norm(r, &beta));
+            record(it_base + it, beta / nu, RBF_HIST_INNER);
         }
         *iters = it;
         *est = beta;
@@ -298,9 +315,17 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
     if (st == RBF_OK) st = rbf_alloc(&ls, n);
     if (st == RBF_OK) st = rbf_alloc(&ax, n);
     if (st == RBF_OK) st = rbf_alloc(&dl, n);
+    double *lbest = nullptr;
+    if (st == RBF_OK && opts->precond == 1) st = rbf_alloc(&lbest, n);
+    sv.t0 = t0;
+    if (opts->history_host && opts->history_cap > 0) {
+        sv.hist = opts->history_host;
+        sv.hist_cap = opts->history_cap;
+    }
     int total_it = 0, refinements = 0, status = RBF_OK;
     double worst = 0.0;
     const int bs = 256, gb = ceil_div(n, bs);
+    const double floor_inner = opts->inner_prec == RBF_FP32 ? 2e-6 : 0.0;
     for (int c = 0; c < nrhs && st == RBF_OK; ++c) {
         const double *uc = u + (int64_t)c * n;
         double *lc = lambda + (int64_t)c * n;
@@ -310,18 +335,95 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
         st = sv.norm(us, &nu);
         if (st != RBF_OK) break;
         if (nu == 0.0) nu = 1.0;
+        sv.nu = nu;
         double rel = INFINITY, prev = INFINITY;
         int it_c = 0, k = 0;
         bool conv = false;
         sv.use_p = opts->precond == 1;
         bool last_used_p = false;
-        while (k < opts->max_refine) {
-            // true residual with the FP64 product
-            if ((st = sv.matvec(RBF_FP64, ls, ax)) != RBF_OK) break;
+        bool stale = true;  // lambda changed since the last FP64 residual
+        // FP64 residual r = u - A64 lambda into sv.r; its relative norm into *out
+        auto fp64_resid = [&](double *out_rel, double *out_norm) -> int {
+            RBF_TRY(sv.matvec(RBF_FP64, ls, ax));
             k_sub<<<gb, bs, 0, s>>>(us, ax, sv.r, n);
+            RBF_LAUNCH_CHECK();
+            RBF_TRY(sv.norm(sv.r, out_norm));
+            *out_rel = *out_norm / nu;
+            sv.record(total_it + it_c, *out_rel, RBF_HIST_FP64);
+            stale = false;
+            return RBF_OK;
+        };
+        // one correction step: GMRES on A (P) y = r (r in sv.r, FP64 norm rn),
+        // lambda += (P) y; at most `budget` inner iterations
+        auto correct = [&](double rn, double rel_now, int budget) -> int {
+            const double eta = std::max(0.5 * opts->rtol / rel_now, floor_inner);
+            RBF_CUDA_TRY(cudaMemsetAsync(dl, 0, n * sizeof(double), s));
+            double *rr = ax;  // keep r: gmres reuses sv.r
+            RBF_CUDA_TRY(cudaMemcpyAsync(rr, sv.r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            int its = 0;
+            double est = 0.0;
+            sv.it_base = total_it + it_c;
+            RBF_TRY(sv.gmres(opts->inner_prec, rr, dl, true, eta * rn, budget, &its, &est));
+            it_c += its;
+            ++refinements;
+            stale = true;
+            last_used_p = sv.use_p;
+            if (sv.use_p) {
+                RBF_TRY(rbf_precond_apply_sorted(t, dl, sv.w, s));
+                k_axpy<<<gb, bs, 0, s>>>(1.0, sv.w, ls, n);
+            } else {
+                k_axpy<<<gb, bs, 0, s>>>(1.0, dl, ls, n);
+            }
+            RBF_LAUNCH_CHECK();
+            return its;
+        };
+        if (sv.use_p) {
+            // Trial of the preconditioner: one restart cycle with P.  When the inner
+            // solve does not converge within that cycle, one plain cycle from the same
+            // start is compared with it on the FP64 residual and the better iterate is
+            // kept; a useless P so costs at most one cycle.
             double rn = 0.0;
-            if ((st = sv.norm(sv.r, &rn)) != RBF_OK) break;
-            rel = rn / nu;
+            if ((st = fp64_resid(&rel, &rn)) != RBF_OK) break;
+            if (rel <= opts->rtol) {
+                conv = true;
+            } else {
+                RBF_CUDA_TRY(cudaMemcpyAsync(lprev, ls, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                const double rel0 = rel, rn0 = rn;
+                const int budget = std::min(opts->restart_m, opts->max_iters);
+                const int its = correct(rn0, rel0, budget);
+                if (its < 0) { st = its; break; }
+                double rel_p = 0.0, rn_p = 0.0;
+                if ((st = fp64_resid(&rel_p, &rn_p)) != RBF_OK) break;
+                rel = rel_p;
+                const bool inner_converged = its < budget;
+                if (rel_p > opts->rtol && !inner_converged && it_c < opts->max_iters) {
+                    RBF_CUDA_TRY(cudaMemcpyAsync(lbest, ls, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                    RBF_CUDA_TRY(cudaMemcpyAsync(ls, lprev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                    sv.use_p = false;
+                    double rel_r = 0.0, rn_r = 0.0;
+                    if ((st = fp64_resid(&rel_r, &rn_r)) != RBF_OK) break;
+                    const int its2 = correct(rn_r, rel_r, std::min(budget, opts->max_iters - it_c));
+                    if (its2 < 0) { st = its2; break; }
+                    double rel_i = 0.0, rn_i = 0.0;
+                    if ((st = fp64_resid(&rel_i, &rn_i)) != RBF_OK) break;
+                    if (rel_i <= rel_p) {
+                        fallback = 1;  // the plain cycle did better: drop P
+                        rel = rel_i;
+                    } else {
+                        RBF_CUDA_TRY(cudaMemcpyAsync(ls, lbest, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                        sv.use_p = true;
+                        last_used_p = true;
+                        rel = rel_p;
+                    }
+                }
+                prev = rel;
+                if (rel <= opts->rtol) conv = true;
+            }
+        }
+        while (!conv && k < opts->max_refine) {
+            // true residual with the FP64 product
+            double rn = 0.0;
+            if ((st = fp64_resid(&rel, &rn)) != RBF_OK) break;
             if (rel <= opts->rtol) {
                 conv = true;
                 break;
@@ -340,31 +442,22 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
             if (stalled) break;
             prev = rel;
             if (it_c >= opts->max_iters) break;
-            ++refinements;
             ++k;
             RBF_CUDA_TRY(cudaMemcpyAsync(lprev, ls, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-            // inner solve A P y = r, delta = P y
-            const double floor_inner = opts->inner_prec == RBF_FP32 ? 2e-6 : 0.0;
-            const double eta = std::max(0.5 * opts->rtol / rel, floor_inner);
-            RBF_CUDA_TRY(cudaMemsetAsync(dl, 0, n * sizeof(double), s));
-            double *rr = ax;  // keep r: gmres reuses sv.r
-            RBF_CUDA_TRY(cudaMemcpyAsync(rr, sv.r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-            int its = 0;
-            double est = 0.0;
-            // each refinement step gets an equal share of the budget, so that the FP64
-            // residual judges a preconditioned step before the budget is gone
+            // inner solve A P y = r, delta = P y; each refinement step gets an equal
+            // share of the budget, so that the FP64 residual judges every step
             const int share = std::max(opts->restart_m, opts->max_iters / opts->max_refine);
-            const int budget = std::min(opts->max_iters - it_c, share);
-            st = sv.gmres(opts->inner_prec, rr, dl, true, eta * rn, budget, &its, &est);
-            if (st != RBF_OK) break;
-            it_c += its;
-            last_used_p = sv.use_p;
-            if (sv.use_p) {
-                if ((st = rbf_precond_apply_sorted(t, dl, sv.w, s)) != RBF_OK) break;
-                k_axpy<<<gb, bs, 0, s>>>(1.0, sv.w, ls, n);
-            } else {
-                k_axpy<<<gb, bs, 0, s>>>(1.0, dl, ls, n);
+            const int its = correct(rn, rel, std::min(opts->max_iters - it_c, share));
+            if (its < 0) {
+                st = its;
+                break;
             }
+        }
+        if (st == RBF_OK && !conv && stale) {
+            // the budget ended on a correction step: judge the final iterate
+            double rn = 0.0;
+            st = fp64_resid(&rel, &rn);
+            if (st == RBF_OK && rel <= opts->rtol) conv = true;
         }
         if (st != RBF_OK) break;
         total_it += it_c;
@@ -385,7 +478,9 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
     rbf_free(ax);
     rbf_free(dl);
     rbf_free(lprev);
+    rbf_free(lbest);
     if (rep) {
+        rep->history_len = sv.hist_len;
         rep->iters = total_it;
         rep->refinements = refinements;
         rep->used_fallback = fallback;

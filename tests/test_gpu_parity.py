@@ -207,3 +207,49 @@ def test_auto_box_and_bad_arguments(rbf):
         rbf.fmm_matvec(t, O.IMQ, 2.0, _dev(lam), u, M=16, period_L=1.5 * info["side"])  # L < 2 side with taper
     with pytest.raises(rbf.RbfError):
         rbf.fmm_matvec(t, O.IMQ, 2.0, _dev(lam), u, M=16, csample=0)  # closed form is Gaussian-only
+
+
+@pytest.mark.parametrize("d,n,D,eps,kernel", [(3, 20000, 3, 77.0, O.GAUSSIAN),
+                                              (2, 30000, 4, 120.0, O.GAUSSIAN),
+                                              (3, 8000, 2, 4.5, O.WENDLAND)])
+def test_near_field_only_product(rbf, d, n, D, eps, kernel):
+    """M = 0: no far field.  The product is the oracle's near-field sum
+    u_i = sum_{j in N(i)} lambda_j Phi(x_i - x_j) (FP64 <= 1e-12, FP32 <= 5e-6,
+    element-wise too), and it is within max_far |Phi| * sum |lambda| of the
+    direct sum (the Lemma bound of Eq. (33) with K = 0).  For these kernels
+    Phi has fallen below 1e-15 at the nearest far offset (one leaf width), so
+    the far field is exactly negligible; rbf_kernel_error reports that value."""
+    import torch
+    from paper_1606_07652_gb300 import _lib
+    X, lam = workloads.uniform(n, d, seed=n + d)
+    T = O.tree(X, np.zeros(d), 1.0, D)
+    ls = lam[T["perm"]]
+    near_sorted = O.p2p(T, ls, kernel, eps)
+    ref = np.empty(n)
+    ref[T["perm"]] = near_sorted
+    t = rbf.tree_build(_dev(X), lo=np.zeros(d), side=1.0, depth=D)
+    lam_d = _dev(lam)
+    out = {}
+    for prec in (rbf.FP64, rbf.FP32):
+        u = torch.empty_like(lam_d)
+        rbf.fmm_matvec(t, kernel, eps, lam_d, u, prec=prec, M=0)
+        torch.cuda.synchronize()
+        out[prec] = u.cpu().numpy()
+    e64, e32 = rel(out[rbf.FP64], ref), rel(out[rbf.FP32], ref)
+    print(f"near-field only d={d} eps={eps}: fp64 {e64:.2e} fp32 {e32:.2e}")
+    assert e64 <= FP64_TOL and e32 <= FP32_TOL
+    w = 1.0 / (1 << D)
+    kerr = _lib.kernel_error(kernel, eps, d, 0, 4.0, 0.0, 1.0, D)
+    assert kerr == pytest.approx(float(O.phi(kernel, eps, np.array([w]))[0]), rel=1e-12, abs=1e-300)
+    assert kerr < 1e-15
+    tg = np.arange(0, n, 97)
+    ud = O.direct(X, lam, kernel, eps, tg)
+    assert np.max(np.abs(out[rbf.FP64][tg] - ud)) <= kerr * np.sum(np.abs(lam)) + 1e-12 * np.max(np.abs(ud))
+
+
+def test_autotune_picks_no_far_field_for_narrow_kernels(rbf):
+    from paper_1606_07652_gb300 import _lib
+    narrow = _lib.autotune(O.GAUSSIAN, 77.0, 3, 1 << 18, 1e-10)
+    assert narrow["M"] == 0 and narrow["err"] <= 1e-10, narrow
+    wide = _lib.autotune(O.GAUSSIAN, 3.0, 3, 1 << 18, 1e-8)
+    assert wide["M"] >= 8, wide
