@@ -342,6 +342,7 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
         sv.use_p = opts->precond == 1;
         bool last_used_p = false;
         bool stale = true;  // lambda changed since the last FP64 residual
+        double last_rn = 0.0;  // ||r|| of that residual (r itself is in sv.r)
         // FP64 residual r = u - A64 lambda into sv.r; its relative norm into *out
         auto fp64_resid = [&](double *out_rel, double *out_norm) -> int {
             RBF_TRY(sv.matvec(RBF_FP64, ls, ax));
@@ -351,6 +352,7 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
             *out_rel = *out_norm / nu;
             sv.record(total_it + it_c, *out_rel, RBF_HIST_FP64);
             stale = false;
+            last_rn = *out_norm;
             return RBF_OK;
         };
         // one correction step: GMRES on A (P) y = r (r in sv.r, FP64 norm rn),
@@ -414,6 +416,7 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
                         sv.use_p = true;
                         last_used_p = true;
                         rel = rel_p;
+                        stale = true;  // sv.r holds the plain iterate's residual
                     }
                 }
                 prev = rel;
@@ -421,9 +424,10 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
             }
         }
         while (!conv && k < opts->max_refine) {
-            // true residual with the FP64 product
-            double rn = 0.0;
-            if ((st = fp64_resid(&rel, &rn)) != RBF_OK) break;
+            // true residual with the FP64 product (kept from the trial when the
+            // iterate has not changed since)
+            double rn = last_rn;
+            if (stale && (st = fp64_resid(&rel, &rn)) != RBF_OK) break;
             if (rel <= opts->rtol) {
                 conv = true;
                 break;
@@ -436,6 +440,7 @@ extern "C" int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps,
                 sv.use_p = false;
                 last_used_p = false;
                 fallback = 1;
+                stale = true;
                 prev = INFINITY;  // the restored iterate starts a fresh progress test
                 continue;
             }

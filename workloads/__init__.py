@@ -92,3 +92,11 @@ def uniform(n, d, seed):
     X = _dedup(rng.random((n, d)))
     lam = rng.standard_normal(len(X))
     return X, lam
+
+
+def jittered_grid(n1, d, seed, jitter=0.3):
+    """Quasi-uniform centres: the n1^d cell centres of a regular grid on [0,1]^d, each
+    moved by a uniform offset of at most jitter/2 cells per coordinate (seeded)."""
+    rng = np.random.default_rng(seed)
+    g = np.stack(np.meshgrid(*[np.arange(n1)] * d, indexing="ij"), -1).reshape(-1, d)
+    return (g + 0.5 + jitter * rng.uniform(-0.5, 0.5, g.shape)) / n1
