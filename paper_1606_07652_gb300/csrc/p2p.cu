@@ -76,6 +76,44 @@ int with_kernel(int kernel, F f)
     }
 }
 
+// The source ranges of a target leaf's neighbours (near list entries e0 ..
+// e0 + ne - 1): rstart[e] = first point of neighbour e, rpre[e] = points of the
+// neighbours before it, rpre[ne] = all of them.  Warp 0 loads 32 entries at a
+// time in parallel and prefix-sums their lengths with shuffles, so the
+// neighbour loads are in flight together.  Ends with __syncthreads().
+__device__ __forceinline__ void near_ranges(int e0, int ne, const int32_t *near_idx,
+                                            const int32_t *leaf_off, int32_t *rstart,
+                                            int32_t *rlen, int32_t *rpre)
+{
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int carry = 0;
+        for (int c0 = 0; c0 < ne; c0 += 32) {
+            const int e = c0 + lane;
+            int st = 0, len = 0;
+            if (e < ne) {
+                const int b = near_idx[e0 + e];
+                st = leaf_off[b];
+                len = leaf_off[b + 1] - st;
+            }
+            int inc = len;  // inclusive scan over the lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            if (e < ne) {
+                rstart[e] = st;
+                if (rlen) rlen[e] = len;
+                rpre[e] = carry + inc - len;
+            }
+            carry += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) rpre[ne] = carry;
+    }
+    __syncthreads();
+}
+
 template <typename R, int DIM, int TG, int KER>
 __global__ void __launch_bounds__(P2P_THREADS) k_p2p(R e2, int64_t N, const R *xs,
                                                      const R *lam, const int32_t *leaf_off,
@@ -94,18 +132,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(R e2, int64_t N, const R *x
     const int a = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int e0 = near_off[a], ne = near_off[a + 1] - e0;
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int e = 0; e < ne; ++e) {
-            int b = near_idx[e0 + e];
-            rstart[e] = leaf_off[b];
-            rlen[e] = leaf_off[b + 1] - leaf_off[b];
-            rpre[e] = run;
-            run += rlen[e];
-        }
-        rpre[ne] = run;
-    }
-    __syncthreads();
+    near_ranges(e0, ne, near_idx, leaf_off, rstart, rlen, rpre);
     const int nsrc = rpre[ne];
     const int t0 = leaf_off[a], nt = leaf_off[a + 1] - t0;
     for (int tb = 0; tb < nt; tb += TB) {
@@ -223,6 +250,151 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(R e2, int64_t N, const R *x
     }
 }
 
+// Leaves of at most P2P_THREADS points: the CTA's threads are (target, source
+// split) pairs, nsplit = floor(P2P_THREADS / nt) splits of the staged sources,
+// so that nearly every lane works whatever the leaf size and the sources are
+// staged once.  Thread tid takes target tid % nt and split tid / nt; the lanes
+// of a warp mostly share a split and so read the same staged source (one
+// broadcast).  Split k takes the sources j = k, k + nsplit, ... of each chunk,
+// SU at a time with independent partial sums; the partial sums of a target
+// are added over the splits in a fixed order.
+template <typename R, int DIM, int KER>
+__global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, const R *xs,
+                                                           const R *lam, const int32_t *leaf_off,
+                                                           const int32_t *near_off,
+                                                           const int32_t *near_idx, R *u)
+{
+    using S4 = typename Src4<R>::type;
+    constexpr int REC = DIM <= 3 ? 1 : 2;
+    constexpr int P2P_SCHUNK = P2P_STAGE_BYTES / (int)(sizeof(S4) * REC);
+    constexpr int SU = RBF_P2P_SU;
+    __shared__ S4 src[P2P_SCHUNK * REC];
+    __shared__ int32_t rstart[729], rpre[730];
+    __shared__ R red[P2P_THREADS];
+    const int a = blockIdx.x;
+    const int e0 = near_off[a], ne = near_off[a + 1] - e0;
+    near_ranges(e0, ne, near_idx, leaf_off, rstart, nullptr, rpre);
+    const int nsrc = rpre[ne];
+    const int t0 = leaf_off[a], nt = leaf_off[a + 1] - t0;  // 1 <= nt <= P2P_THREADS
+    const int nsplit = P2P_THREADS / nt;
+    const int tgt = threadIdx.x % nt, sp = threadIdx.x / nt;
+    const bool active = sp < nsplit;
+    R xt[DIM];
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) xt[t] = xs[(int64_t)t * N + t0 + tgt];
+    R acc[SU];
+#pragma unroll
+    for (int k = 0; k < SU; ++k) acc[k] = (R)0;
+    for (int s0 = 0; s0 < nsrc; s0 += P2P_SCHUNK) {
+        const int cnt = min(P2P_SCHUNK, nsrc - s0);
+        __syncthreads();
+        for (int v = threadIdx.x; v < cnt; v += P2P_THREADS) {
+            const int vv = s0 + v;
+            int lo = 0, hi = ne - 1;
+            while (lo < hi) {  // last range with rpre[e] <= vv
+                const int mid = (lo + hi + 1) >> 1;
+                if (rpre[mid] <= vv) lo = mid;
+                else hi = mid - 1;
+            }
+            const int64_t j = rstart[lo] + (vv - rpre[lo]);
+            R c[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
+#pragma unroll
+            for (int t = 0; t < DIM; ++t) c[t] = xs[(int64_t)t * N + j];
+            S4 r0;
+            r0.x = c[0];
+            r0.y = c[1];
+            r0.z = c[2];
+            r0.w = lam[j];
+            src[REC * v] = r0;
+            if (REC == 2) {
+                S4 r1;
+                r1.x = c[3];
+                r1.y = c[4];
+                r1.z = c[5];
+                r1.w = (R)0;
+                src[REC * v + 1] = r1;
+            }
+        }
+        __syncthreads();
+        if (!active) continue;
+        // steps whose SU sources all lie in the chunk need no masks; one masked
+        // step takes the rest
+        auto step = [&](int j0, bool masked) {
+#pragma unroll
+            for (int k = 0; k < SU; ++k) {
+                const int jj = j0 + k * nsplit;
+                const int j = masked ? min(jj, cnt - 1) : jj;
+                const S4 r0 = src[REC * j];
+                S4 r1;
+                if (REC == 2) r1 = src[REC * j + 1];
+                const R wgt = !masked || jj < cnt ? r0.w : (R)0;
+                R d0 = xt[0] - r0.x;
+                R r2 = d0 * d0;
+                if (DIM > 1) {
+                    R d1 = xt[DIM > 1 ? 1 : 0] - r0.y;
+                    r2 = fma(d1, d1, r2);
+                }
+                if (DIM > 2) {
+                    R d2 = xt[DIM > 2 ? 2 : 0] - r0.z;
+                    r2 = fma(d2, d2, r2);
+                }
+                if (DIM > 3) {
+                    R d3 = xt[DIM > 3 ? 3 : 0] - r1.x;
+                    r2 = fma(d3, d3, r2);
+                }
+                if (DIM > 4) {
+                    R d4 = xt[DIM > 4 ? 4 : 0] - r1.y;
+                    r2 = fma(d4, d4, r2);
+                }
+                if (DIM > 5) {
+                    R d5 = xt[DIM > 5 ? 5 : 0] - r1.z;
+                    r2 = fma(d5, d5, r2);
+                }
+                acc[k] = fma(wgt, phi_r2<KER>(e2, r2), acc[k]);
+            }
+        };
+        int j0 = sp;
+        for (; j0 + (SU - 1) * nsplit < cnt; j0 += SU * nsplit) step(j0, false);
+        if (j0 < cnt) step(j0, true);
+    }
+    R tsum = acc[0];
+#pragma unroll
+    for (int k = 1; k < SU; ++k) tsum += acc[k];
+    red[threadIdx.x] = active ? tsum : (R)0;
+    __syncthreads();
+    if (threadIdx.x < nt) {
+        R sum = red[threadIdx.x];
+        for (int k = 1; k < nsplit; ++k) sum += red[k * nt + threadIdx.x];
+        u[t0 + threadIdx.x] = sum;
+    }
+}
+
+template <typename R, int KER>
+int launch_p2p_split(int d, R e2, const rbf_tree *t, const R *xs, const R *lam, R *u,
+                     cudaStream_t s)
+{
+    const int nleaf = t->nleaf();
+    switch (d) {
+#define RBF_P2P_CASE(DD)                                                                          \
+    case DD:                                                                                      \
+        k_p2p_split<R, DD, KER><<<nleaf, P2P_THREADS, 0, s>>>(e2, t->N, xs, lam, t->leaf_off,      \
+                                                              t->near_off, t->near_idx, u);        \
+        break;
+        RBF_P2P_CASE(1)
+        RBF_P2P_CASE(2)
+        RBF_P2P_CASE(3)
+        RBF_P2P_CASE(4)
+        RBF_P2P_CASE(5)
+        RBF_P2P_CASE(6)
+#undef RBF_P2P_CASE
+        default:
+            rbf_set_error("p2p: unsupported dimension %d", d);
+            return RBF_EINVAL;
+    }
+    RBF_LAUNCH_CHECK();
+    return RBF_OK;
+}
+
 template <typename R, int TG, int KER>
 int launch_p2p_tg(int d, R e2, const rbf_tree *t, const R *xs, const R *lam, R *u, cudaStream_t s)
 {
@@ -248,13 +420,18 @@ int launch_p2p_tg(int d, R e2, const rbf_tree *t, const R *xs, const R *lam, R *
     return RBF_OK;
 }
 
-// target groups of 32 per pass: one for small leaves (a leaf of up to 64 points takes
-// two passes rather than a half-empty second group), four for large leaves
+// leaves of up to P2P_THREADS points: the split kernel; larger ones: target groups of
+// 32 per pass (four per pass for large leaves)
 template <typename R>
 int launch_p2p(int d, int kernel, R e2, const rbf_tree *t, const R *xs, const R *lam, R *u,
                cudaStream_t s)
 {
     const int ml = std::max<int>(1, t->max_leaf);
+    // leaves of at most one CTA of points: (target, source split) threads
+    if (ml <= P2P_THREADS)
+        return with_kernel(kernel, [&](auto K) {
+            return launch_p2p_split<R, decltype(K)::value>(d, e2, t, xs, lam, u, s);
+        });
     const bool small = ml <= RBF_P2P_SMALL || RBF_P2P_TGMAX == 1;
     return with_kernel(kernel, [&](auto K) {
         return small ? launch_p2p_tg<R, 1, decltype(K)::value>(d, e2, t, xs, lam, u, s)
@@ -295,17 +472,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_multi(float e2, int64_t N,
     const int a = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int e0 = near_off[a], ne = near_off[a + 1] - e0;
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int e = 0; e < ne; ++e) {
-            const int b = near_idx[e0 + e];
-            rstart[e] = leaf_off[b];
-            rpre[e] = run;
-            run += leaf_off[b + 1] - leaf_off[b];
-        }
-        rpre[ne] = run;
-    }
-    __syncthreads();
+    near_ranges(e0, ne, near_idx, leaf_off, rstart, nullptr, rpre);
     const int nsrc = rpre[ne];
     const int t0 = leaf_off[a], nt = leaf_off[a + 1] - t0;
     for (int tb = 0; tb < nt; tb += TB) {
