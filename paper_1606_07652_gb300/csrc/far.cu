@@ -82,6 +82,11 @@
 #endif
 // L2P partial sums: 1 = one shared-memory slot per thread and point, reduced
 // once per chunk; 0 = warp shuffles per point
+// FP32 3-D grouped coupling: modes per thread (1 or 2; two need 141 registers and ran
+// slower, 3.53 against 3.42 ms at the 3-D M = 32 product)
+#ifndef RBF_M2L_MP
+#define RBF_M2L_MP 1
+#endif
 #ifndef RBF_L2P_SMEMRED
 #define RBF_L2P_SMEMRED 1
 #endif
@@ -880,48 +885,57 @@ __global__ void k_m2l(int d, int M, int D, int n1, int64_t nmode, int64_t ms, co
 //     S_a = sum_{delta in {-1,0,1}^d} prod_t Q_t^{delta_t} V_{a+delta},  Q_t = e^{-i xi_t w_D}
 // is summed one dimension at a time over the block, so each neighbour
 // expansion is read once per CTA instead of once per target.
-template <typename R, int DIM>
+template <typename R, int DIM, int MP>
 __global__ void __launch_bounds__(128) k_m2l_grp(int M, int D, int n1, int nmode, int64_t ms,
                                                  const cplx<R> *shD,
                                                  const R *omegaC, const cplx<R> *root_ph,
                                                  const uint64_t *parent_key, const int32_t *nb4,
-                                                 const cplx<R> *V0, const cplx<R> *VD, cplx<R> *Lx)
+                                                 const cplx<R> *V0, const cplx<R> *VD,
+                                                 const cplx<R> *Vzero, cplx<R> *Lx)
 {
+    // MP consecutive modes per thread (2: one 16-byte load of two FP32 modes)
     using C = cplx<R>;
     constexpr int NB = DIM == 1 ? 4 : (DIM == 2 ? 16 : 64);
-    __shared__ const C *base[NB];   // expansion of each block position, or null
+    __shared__ const C *base[NB];   // expansion of each block position (absent: zeros)
     __shared__ int32_t nb[NB];
     const int p = blockIdx.x;
     for (int q = threadIdx.x; q < NB; q += blockDim.x) {
         const int32_t b = nb4[(int64_t)p * NB + q];
         nb[q] = b;
-        base[q] = b >= 0 ? VD + (int64_t)b * ms : nullptr;
+        base[q] = b >= 0 ? VD + (int64_t)b * ms : Vzero;
     }
     __syncthreads();
-    const int m = blockIdx.y * blockDim.x + threadIdx.x;
-    if (m >= nmode) return;
-    int kidx[3] = {0, 0, 0};
-    {
-        int r = m;
+    const int m0 = MP * (blockIdx.y * blockDim.x + threadIdx.x);
+    if (m0 >= nmode) return;
+    // the second mode of an odd last pair reads the zero padding of the stride
+    int kidx[MP][3];
+    C Q[MP][3];
+#pragma unroll
+    for (int e = 0; e < MP; ++e) {
+        int r = min(m0 + e, nmode - 1);
+        for (int t = 0; t < 3; ++t) kidx[e][t] = 0;
         for (int t = DIM - 1; t >= 1; --t) {
-            kidx[t] = r % n1;
+            kidx[e][t] = r % n1;
             r /= n1;
         }
-        kidx[0] = r + M / 2;
-    }
-    // Q_t = e^{-i xi_k w_D} = (e^{-i xi_k w_D / 2})^2 from the plan's half-shift table
-    C Q[3];
+        kidx[e][0] = r + M / 2;
+        // Q_t = e^{-i xi_k w_D} = (e^{-i xi_k w_D / 2})^2 from the plan's half-shift table
 #pragma unroll
-    for (int t = 0; t < DIM; ++t) {
-        const C hq = shD[kidx[t]];
-        Q[t] = cmul(hq, hq);
+        for (int t = 0; t < DIM; ++t) {
+            const C hq = shD[kidx[e][t]];
+            Q[e][t] = cmul(hq, hq);
+        }
     }
-    auto ld = [&](int pos) -> C {
-        const C *bp = base[pos];
-        if (bp) return bp[m];
-        C z;
-        z.x = z.y = (R)0;
-        return z;
+    auto ld = [&](int pos, C (&v)[MP]) {
+        const C *bp = base[pos] + m0;
+        if constexpr (MP == 2 && sizeof(R) == 4) {
+            const float4 w = *reinterpret_cast<const float4 *>(bp);
+            v[0] = make_float2(w.x, w.y);
+            v[1] = make_float2(w.z, w.w);
+        } else {
+#pragma unroll
+            for (int e = 0; e < MP; ++e) v[e] = bp[e];
+        }
     };
     // 3-tap sum for targets at block positions 1 and 2 of a line v[0..3]
     auto tap = [&](const C *v, C q, C *out) {
@@ -933,63 +947,86 @@ __global__ void __launch_bounds__(128) k_m2l_grp(int M, int D, int n1, int nmode
             out[j] = s;
         }
     };
-    C S[8];  // targets, index j0 + 2 j1 + 4 j2 (j_t = 0, 1 <-> block position 1, 2)
+    C S[MP][8];  // targets, index j0 + 2 j1 + 4 j2 (j_t = 0, 1 <-> block position 1, 2)
     if (DIM == 1) {
-        C v[4];
+        C v[MP][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = ld(i);
-        tap(v, Q[0], S);
+        for (int i = 0; i < 4; ++i) {
+            C w[MP];
+            ld(i, w);
+#pragma unroll
+            for (int e = 0; e < MP; ++e) v[e][i] = w[e];
+        }
+#pragma unroll
+        for (int e = 0; e < MP; ++e) tap(v[e], Q[e][0], S[e]);
     } else if (DIM == 2) {
-        C s1[4][2];  // [i1][j0]
 #pragma unroll
-        for (int i1 = 0; i1 < 4; ++i1) {
-            C v[4];
-#pragma unroll
-            for (int i0 = 0; i0 < 4; ++i0) v[i0] = ld(i0 + 4 * i1);
-            tap(v, Q[0], s1[i1]);
-        }
-#pragma unroll
-        for (int j0 = 0; j0 < 2; ++j0) {
-            C v[4], o[2];
-#pragma unroll
-            for (int i1 = 0; i1 < 4; ++i1) v[i1] = s1[i1][j0];
-            tap(v, Q[1], o);
-            S[j0] = o[0];
-            S[j0 + 2] = o[1];
-        }
-    } else {
-        C s2[4][2][2];  // [i2][j1][j0]
-#pragma unroll
-        for (int i2 = 0; i2 < 4; ++i2) {
+        for (int e = 0; e < MP; ++e) {
             C s1[4][2];  // [i1][j0]
 #pragma unroll
             for (int i1 = 0; i1 < 4; ++i1) {
                 C v[4];
 #pragma unroll
-                for (int i0 = 0; i0 < 4; ++i0) v[i0] = ld(i0 + 4 * i1 + 16 * i2);
-                tap(v, Q[0], s1[i1]);
+                for (int i0 = 0; i0 < 4; ++i0) {
+                    C w[MP];
+                    ld(i0 + 4 * i1, w);
+                    v[i0] = w[e];
+                }
+                tap(v, Q[e][0], s1[i1]);
             }
 #pragma unroll
             for (int j0 = 0; j0 < 2; ++j0) {
                 C v[4], o[2];
 #pragma unroll
                 for (int i1 = 0; i1 < 4; ++i1) v[i1] = s1[i1][j0];
-                tap(v, Q[1], o);
-                s2[i2][0][j0] = o[0];
-                s2[i2][1][j0] = o[1];
+                tap(v, Q[e][1], o);
+                S[e][j0] = o[0];
+                S[e][j0 + 2] = o[1];
             }
         }
+    } else {
+        C s2[MP][4][2][2];  // [mode][i2][j1][j0]
 #pragma unroll
-        for (int j1 = 0; j1 < 2; ++j1)
+        for (int i2 = 0; i2 < 4; ++i2) {
+            C s1[MP][4][2];  // [mode][i1][j0]
 #pragma unroll
-            for (int j0 = 0; j0 < 2; ++j0) {
-                C v[4], o[2];
+            for (int i1 = 0; i1 < 4; ++i1) {
+                C v[MP][4];
 #pragma unroll
-                for (int i2 = 0; i2 < 4; ++i2) v[i2] = s2[i2][j1][j0];
-                tap(v, Q[2], o);
-                S[j0 + 2 * j1] = o[0];
-                S[j0 + 2 * j1 + 4] = o[1];
+                for (int i0 = 0; i0 < 4; ++i0) {
+                    C w[MP];
+                    ld(i0 + 4 * i1 + 16 * i2, w);
+#pragma unroll
+                    for (int e = 0; e < MP; ++e) v[e][i0] = w[e];
+                }
+#pragma unroll
+                for (int e = 0; e < MP; ++e) tap(v[e], Q[e][0], s1[e][i1]);
             }
+#pragma unroll
+            for (int e = 0; e < MP; ++e)
+#pragma unroll
+                for (int j0 = 0; j0 < 2; ++j0) {
+                    C v[4], o[2];
+#pragma unroll
+                    for (int i1 = 0; i1 < 4; ++i1) v[i1] = s1[e][i1][j0];
+                    tap(v, Q[e][1], o);
+                    s2[e][i2][0][j0] = o[0];
+                    s2[e][i2][1][j0] = o[1];
+                }
+        }
+#pragma unroll
+        for (int e = 0; e < MP; ++e)
+#pragma unroll
+            for (int j1 = 0; j1 < 2; ++j1)
+#pragma unroll
+                for (int j0 = 0; j0 < 2; ++j0) {
+                    C v[4], o[2];
+#pragma unroll
+                    for (int i2 = 0; i2 < 4; ++i2) v[i2] = s2[e][i2][j1][j0];
+                    tap(v, Q[e][2], o);
+                    S[e][j0 + 2 * j1] = o[0];
+                    S[e][j0 + 2 * j1 + 4] = o[1];
+                }
     }
     // targets: L_a = omega C (e^{i xi.(c_a - c_0)} V_0 - S_a)
     int kp[3] = {0, 0, 0};
@@ -1000,13 +1037,20 @@ __global__ void __launch_bounds__(128) k_m2l_grp(int M, int D, int n1, int nmode
             for (int t = 0; t < DIM; ++t) kp[t] |= (int)((key >> (b * DIM + t)) & 1u) << b;
     }
     const int64_t nk = (int64_t)1 << D;
-    C rp[3][2];
+    C rp[MP][3][2];
+    C v0[MP];
+    R w[MP];
 #pragma unroll
-    for (int t = 0; t < DIM; ++t)
+    for (int e = 0; e < MP; ++e) {
+        const int m = min(m0 + e, nmode - 1);
 #pragma unroll
-        for (int j = 0; j < 2; ++j) rp[t][j] = root_ph[((int64_t)t * nk + 2 * kp[t] + j) * n1 + kidx[t]];
-    const C v0 = V0[m];
-    const R w = omegaC[m];
+        for (int t = 0; t < DIM; ++t)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                rp[e][t][j] = root_ph[((int64_t)t * nk + 2 * kp[t] + j) * n1 + kidx[e][t]];
+        v0[e] = V0[m];
+        w[e] = m0 + e < nmode ? omegaC[m] : (R)0;  // the padding mode gets zero
+    }
 #pragma unroll
     for (int c = 0; c < (1 << DIM); ++c) {
         int pos = 0;
@@ -1014,14 +1058,24 @@ __global__ void __launch_bounds__(128) k_m2l_grp(int M, int D, int n1, int nmode
         for (int t = 0; t < DIM; ++t) pos += (((c >> t) & 1) + 1) << (2 * t);
         const int a = nb[pos];
         if (a < 0) continue;
-        C ph = rp[0][c & 1];
+        C out[MP];
 #pragma unroll
-        for (int t = 1; t < DIM; ++t) ph = cmul(ph, rp[t][(c >> t) & 1]);
-        C r = cmul(ph, v0);
-        C out;
-        out.x = w * (r.x - S[c].x);
-        out.y = w * (r.y - S[c].y);
-        Lx[(int64_t)a * ms + m] = out;
+        for (int e = 0; e < MP; ++e) {
+            C ph = rp[e][0][c & 1];
+#pragma unroll
+            for (int t = 1; t < DIM; ++t) ph = cmul(ph, rp[e][t][(c >> t) & 1]);
+            const C r = cmul(ph, v0[e]);
+            out[e].x = w[e] * (r.x - S[e][c].x);
+            out[e].y = w[e] * (r.y - S[e][c].y);
+        }
+        C *dst = Lx + (int64_t)a * ms + m0;
+        if constexpr (MP == 2 && sizeof(R) == 4) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(out[0].x, out[0].y, out[1].x, out[1].y);
+        } else {
+#pragma unroll
+            for (int e = 0; e < MP; ++e)
+                if (m0 + e < nmode) dst[e] = out[e];
+        }
     }
 }
 
@@ -1278,15 +1332,20 @@ int rbf_run_m2l(rbf_tree *t, const rbf_plan *p, const cplx<R> *VD, cplx<R> *L, c
     const C *V0 = (const C *)p->V[0];
     if (d <= 3) {
         const int gb = 128;
-        dim3 grid(t->lev[D - 1].nbox, ceil_div(p->nmode, gb));
-#define RBF_M2L_GRP(DD)                                                                            \
-    k_m2l_grp<R, DD><<<grid, gb, 0, s>>>(p->M, D, p->n1, (int)p->nmode, p->mstride,                \
-                                         (const C *)p->shift_ph + (int64_t)D * p->n1,                \
-                                         (const R *)p->omegaC, (const C *)p->root_ph,                \
-                                         t->lev[D - 1].key, t->nb4, V0, VD, L)
-        if (d == 1) RBF_M2L_GRP(1);
-        else if (d == 2) RBF_M2L_GRP(2);
-        else RBF_M2L_GRP(3);
+#define RBF_M2L_GRP(DD, MP)                                                                        \
+    k_m2l_grp<R, DD, MP><<<dim3(t->lev[D - 1].nbox, ceil_div(p->nmode, gb * MP)), gb, 0, s>>>(      \
+        p->M, D, p->n1, (int)p->nmode, p->mstride, (const C *)p->shift_ph + (int64_t)D * p->n1,     \
+        (const R *)p->omegaC, (const C *)p->root_ph, t->lev[D - 1].key, t->nb4, V0, VD,             \
+        (const C *)p->Vzero, L)
+        // FP32 in 3-D: RBF_M2L_MP modes per thread
+        if (d == 1) {
+            RBF_M2L_GRP(1, 1);
+        } else if (d == 2) {
+            RBF_M2L_GRP(2, 1);
+        } else {
+            if constexpr (sizeof(R) == 4) RBF_M2L_GRP(3, RBF_M2L_MP);
+            else RBF_M2L_GRP(3, 1);
+        }
 #undef RBF_M2L_GRP
         RBF_LAUNCH_CHECK();
     } else if (D >= 2 && D <= 4 && d * D <= 12) {

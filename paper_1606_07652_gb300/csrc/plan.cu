@@ -179,6 +179,7 @@ void rbf_plan_free(rbf_plan *p)
     rbf_free(p->shift_ph);
     for (int l = 0; l <= RBF_MAX_DEPTH; ++l) rbf_free(p->V[l]);
     rbf_free(p->Lleaf);
+    rbf_free(p->Vzero);
     rbf_free(p->lam_s);
     rbf_free(p->u_near);
     rbf_free(p->u_far);
@@ -273,6 +274,8 @@ static int alloc_work(rbf_tree *t, rbf_plan *p)
     for (int l = 0; l <= t->D; ++l)
         RBF_TRY(rbf_alloc(reinterpret_cast<cplx<R> **>(&p->V[l]), (size_t)t->lev[l].nbox * p->mstride));
     RBF_TRY(rbf_alloc(reinterpret_cast<cplx<R> **>(&p->Lleaf), (size_t)t->nleaf() * p->mstride));
+    RBF_TRY(rbf_alloc(reinterpret_cast<cplx<R> **>(&p->Vzero), (size_t)p->mstride));
+    RBF_CUDA_TRY(cudaMemset(p->Vzero, 0, (size_t)p->mstride * sizeof(cplx<R>)));
     RBF_TRY(rbf_alloc(reinterpret_cast<R **>(&p->lam_s), t->N));
     RBF_TRY(rbf_alloc(reinterpret_cast<R **>(&p->u_near), t->N));
     RBF_TRY(rbf_alloc(reinterpret_cast<R **>(&p->u_far), t->N));

@@ -205,6 +205,7 @@ struct rbf_plan {
                                // (the square of row D is the leaf-neighbour phase e^{-i xi_k w_D})
     void *V[RBF_MAX_DEPTH + 1] = {nullptr};  // expansions per level
     void *Lleaf = nullptr;     // local expansions at the leaves
+    void *Vzero = nullptr;     // [mstride] zeros: the expansion of an absent box
     void *lam_s = nullptr;     // [N] gathered lambda
     void *u_near = nullptr;    // [N]
     void *u_far = nullptr;     // [N]
