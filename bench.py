@@ -327,6 +327,10 @@ def run_ours(args):
                                                      M=args.mrhs_M)
         if not args.skip_cpu and world == 1:
             out["cpu_baseline"] = cpu_baseline(X, lam, p, budget_s=args.cpu_budget)
+            iters = None
+            if "solve" in out:
+                iters = out["solve"]["n262144"]["fp64_plain"]["iters"]
+            out["cpu_baseline_suite"] = cpu_baseline_suite(iters)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -804,6 +808,86 @@ def cpu_baseline(X, lam, p, budget_s=60.0):
             "sample": f"FP64 oracle MLFMM product on the {len(Xs)} centres of the level-1 box at "
                       f"the origin (same root cube, depth 5, M=32, L=4, alpha=4.5); "
                       f"setup {t1 - t0:.1f} s not timed, product {t2 - t1:.1f} s"}
+
+
+def _box_sample(X, level, pick=None):
+    """Indices of the centres in one level-`level` box of the unit cube: the box at the
+    origin, or the most populated one (pick='max')."""
+    k = np.minimum(np.floor(X * (1 << level)).astype(np.int64), (1 << level) - 1)
+    code = np.zeros(len(X), dtype=np.int64)
+    for t in range(X.shape[1]):
+        code = code * (1 << level) + k[:, t]
+    if pick == "max":
+        target = np.bincount(code).argmax()
+    else:
+        target = 0
+    return np.flatnonzero(code == target)
+
+
+def _timed_oracle(fn, threads):
+    import oracle as O
+    O.set_num_threads(threads)
+    t0 = time.perf_counter()
+    fn()
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_suite(solve_iters=None):
+    """The oracle on the host cores, on all of them and on one, for the configurations
+    of the measurement plan: c1 in full (product and direct sum), c2 on the centres of
+    one level-2 box (same tree and expansion), the c5 direct sum on sampled targets, and
+    c3 as the product on its most populated level-1 box, scaled to the whole workload and
+    multiplied by the GPU solve's iteration count (an estimate: the oracle solve itself
+    would take hours)."""
+    import oracle as O
+    import workloads
+    allc = O.num_threads()
+    out = {"cores_all": allc}
+    # c1: d=2, N=4096, Gaussian eps=4, depth 3, M=32, L=2.5
+    X1, lam1, p1 = workloads.config1()
+    T1 = O.tree(X1, np.zeros(2), 1.0, p1["depth"])
+    wc1 = O.coeffs_sampled(p1["kernel"], p1["eps"], 2, p1["M"], p1["L"], p1["alpha"], 1.0)
+    c1 = {}
+    for tag, th in (("all_cores", allc), ("one_core", 1)):
+        sec = _timed_oracle(lambda: O.fmm(T1, lam1, p1["kernel"], p1["eps"], wc1, p1["M"],
+                                          p1["L"]), th)
+        c1[tag] = {"points_per_s": len(X1) / sec, "seconds": sec}
+    sec = _timed_oracle(lambda: O.direct(X1, lam1, p1["kernel"], p1["eps"]), allc)
+    c1["direct_all_cores"] = {"points_per_s": len(X1) / sec, "seconds": sec}
+    out["c1"] = dict(c1, sample="all 4096 centres")
+    # c2: centres of the level-2 box at the origin, depth 5, M=32, L=4, alpha=4.5
+    X2, lam2, _, p2 = workloads.config2()
+    sel = _box_sample(X2, 2)
+    Xs, ls = X2[sel], lam2[sel]
+    T2 = O.tree(Xs, np.zeros(3), 1.0, p2["depth"])
+    wc2 = O.coeffs_sampled(p2["kernel"], p2["eps"], 3, p2["M"], p2["L"], p2["alpha"], 1.0)
+    c2 = {}
+    for tag, th in (("all_cores", allc), ("one_core", 1)):
+        sec = _timed_oracle(lambda: O.fmm(T2, ls, p2["kernel"], p2["eps"], wc2, p2["M"], p2["L"]), th)
+        c2[tag] = {"points_per_s": len(Xs) / sec, "seconds": sec}
+    out["c2"] = dict(c2, sample="%d centres of the level-2 box at the origin" % len(Xs))
+    # c5: direct sum over all 2^19 centres at sampled targets (the oracle FMM's per-level
+    # coupling is out of reach in 5-D)
+    X5, lam5, _, tg5, p5 = workloads.config5()
+    c5 = {}
+    for tag, th, nt in (("all_cores", allc, 1024), ("one_core", 1, 64)):
+        sec = _timed_oracle(lambda: O.direct(X5, lam5, p5["kernel"], p5["eps"], tg5[:nt]), th)
+        c5[tag] = {"targets_per_s": nt / sec, "pairs_per_s": nt * len(X5) / sec, "seconds": sec}
+    out["c5"] = dict(c5, sample="direct sum over %d centres at 1024 / 64 targets" % len(X5))
+    # c3: product on the most populated level-1 box (depth 6, M=24, L=3), scaled
+    X3, u3, p3 = workloads.config3()
+    sel = _box_sample(X3, 1, pick="max")
+    lam3 = np.random.default_rng(5).standard_normal(len(sel))
+    T3 = O.tree(X3[sel], np.zeros(3), 1.0, 6)
+    wc3 = O.coeffs_sampled(p3["kernel"], p3["eps"], 3, p3["M"], p3["L"], p3["alpha"], 1.0)
+    sec = _timed_oracle(lambda: O.fmm(T3, lam3, p3["kernel"], p3["eps"], wc3, p3["M"], p3["L"]), allc)
+    per = sec * len(X3) / len(sel)
+    out["c3"] = {"sample": "%d centres of the most populated level-1 box" % len(sel),
+                 "sample_seconds": sec, "per_product_estimate_s": per,
+                 "iterations": solve_iters,
+                 "solve_estimate_s": per * solve_iters if solve_iters else None}
+    O.set_num_threads(allc)
+    return out
 
 
 def run_reference(args):

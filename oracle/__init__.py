@@ -90,6 +90,11 @@ def num_threads() -> int:
     return int(lib().orc_num_threads())
 
 
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on (for timing on one core)."""
+    lib().orc_set_num_threads(ctypes.c_int(int(n)))
+
+
 def _p(a):
     # data_as keeps a reference to the array inside the pointer object, so a
     # temporary (a converted copy built in the argument list) stays alive for

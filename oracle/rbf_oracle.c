@@ -386,3 +386,14 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* threads of the following parallel regions (timing of the oracle on 1 core) */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
