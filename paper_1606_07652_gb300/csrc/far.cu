@@ -1446,26 +1446,27 @@ int launch_l2p_horner(const FarArgs<float> &a0, int nleaf, cudaStream_t s)
     return RBF_OK;
 }
 
-// rows of up to 33 columns; an even count runs with one zero column more
+// rows of up to 33 columns: NC = the column count rounded up to odd (at least 3);
+// an even count (one dimension, M = 2 mod 4) runs with one zero column more
 int l2p_horner(const FarArgs<float> &a, int nleaf, cudaStream_t s)
 {
-    switch ((a.ncol + 1) / 2) {
+    switch (a.ncol / 2) {
+        case 0:
         case 1: return launch_l2p_horner<3>(a, nleaf, s);
-        case 2: return launch_l2p_horner<3>(a, nleaf, s);
-        case 3: return launch_l2p_horner<5>(a, nleaf, s);
-        case 4: return launch_l2p_horner<7>(a, nleaf, s);
-        case 5: return launch_l2p_horner<9>(a, nleaf, s);
-        case 6: return launch_l2p_horner<11>(a, nleaf, s);
-        case 7: return launch_l2p_horner<13>(a, nleaf, s);
-        case 8: return launch_l2p_horner<15>(a, nleaf, s);
-        case 9: return launch_l2p_horner<17>(a, nleaf, s);
-        case 10: return launch_l2p_horner<19>(a, nleaf, s);
-        case 11: return launch_l2p_horner<21>(a, nleaf, s);
-        case 12: return launch_l2p_horner<23>(a, nleaf, s);
-        case 13: return launch_l2p_horner<25>(a, nleaf, s);
-        case 14: return launch_l2p_horner<27>(a, nleaf, s);
-        case 15: return launch_l2p_horner<29>(a, nleaf, s);
-        case 16: return launch_l2p_horner<31>(a, nleaf, s);
+        case 2: return launch_l2p_horner<5>(a, nleaf, s);
+        case 3: return launch_l2p_horner<7>(a, nleaf, s);
+        case 4: return launch_l2p_horner<9>(a, nleaf, s);
+        case 5: return launch_l2p_horner<11>(a, nleaf, s);
+        case 6: return launch_l2p_horner<13>(a, nleaf, s);
+        case 7: return launch_l2p_horner<15>(a, nleaf, s);
+        case 8: return launch_l2p_horner<17>(a, nleaf, s);
+        case 9: return launch_l2p_horner<19>(a, nleaf, s);
+        case 10: return launch_l2p_horner<21>(a, nleaf, s);
+        case 11: return launch_l2p_horner<23>(a, nleaf, s);
+        case 12: return launch_l2p_horner<25>(a, nleaf, s);
+        case 13: return launch_l2p_horner<27>(a, nleaf, s);
+        case 14: return launch_l2p_horner<29>(a, nleaf, s);
+        case 15: return launch_l2p_horner<31>(a, nleaf, s);
         default: return launch_l2p_horner<33>(a, nleaf, s);
     }
 }

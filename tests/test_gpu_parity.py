@@ -103,6 +103,10 @@ MATVEC_CASES = [
     ("wendland-2d", 2, 5000, 4, O.WENDLAND, 0.5, 16, 4.0, 0.0, "u"),
     ("wendland-3d-taper", 3, 6000, 3, O.WENDLAND, 3.0, 12, 4.0, 4.5, "u"),
     ("wendland-1d", 1, 2000, 4, O.WENDLAND, 0.5, 16, 4.0, 0.0, "u"),
+    # one dimension has M/2 + 1 columns: even counts (M = 2 mod 4) and the widest row
+    ("1d-4-cols", 1, 2500, 4, O.GAUSSIAN, 2.0, 6, 3.0, 0.0, "u"),
+    ("1d-16-cols", 1, 3000, 5, O.IMQ, 3.0, 30, 4.0, 4.5, "u"),
+    ("1d-32-cols", 1, 2000, 3, O.GAUSSIAN, 3.0, 62, 3.0, 0.0, "u"),
 ]
 
 
