@@ -520,8 +520,11 @@ def kernels_measurement(rbf, dev, n=1 << 20, depths=(4, 5), Ms=(16, 24, 32)):
 
 def batch_measurement(rbf, dev, n_problems=256, steps=5):
     """256 problems, N log-uniform in [2048, 65536], d in {2,3}, Gaussian or IMQ,
-    eps ~ U[1,5], 4 right-hand sides: autotuned batch, one graph launch of all FP32
-    products per step; aggregate points/s = sum_p N_p * nrhs_p / product time."""
+    eps ~ U[1,5], 4 right-hand sides: the cost model sends each problem to the
+    direct sum (one persistent launch for all of them), the near field alone or the
+    FMM; one graph launch of all FP32 products per step; aggregate points/s =
+    sum_p N_p * nrhs_p / product time.  A few lockstep GMRES steps, each one graph
+    launch on the device, give the step time."""
     import torch
     import workloads
     from paper_1606_07652_gb300 import _lib
@@ -551,13 +554,23 @@ def batch_measurement(rbf, dev, n_problems=256, steps=5):
     ud = torch.as_tensor(U, device=dev)
     x = torch.zeros_like(ud)
     rep = B.solve(ud, x, restart_m=20, max_iters=10, rtol=1e-12, prec=rbf.FP32)
+    st = B.stats()
     B.free()
+    tree = lay["depth"] > 0
     return {"problems": n_problems, "systems": int(sum(q["U"].shape[1] for q in probs)),
             "points_x_rhs": int(total), "setup_s": setup,
             "matvec_ms": ms, "value": total / (ms / 1e3), "unit": "points/s (all problems and RHS)",
-            "gmres_step_ms": rep["step_ms"],
-            "M_range": [int(lay["M"].min()), int(lay["M"].max())],
-            "depth_range": [int(lay["depth"].min()), int(lay["depth"].max())]}
+            "gmres_step_ms": rep["step_ms"], "gmres_steps": rep["iters"],
+            "step_over_product": rep["step_ms"] / ms,
+            "choice": {"direct": st["n_direct"], "near_field_only": st["n_near_only"],
+                       "fmm": st["n_fmm"]},
+            "direct_work_items": st["direct_items"],
+            "graph_kernel_nodes": {"product": st["product_nodes"], "gmres_step": st["step_nodes"]},
+            "predicted_ms": st["predicted_ms"], "cost_model_s": st["model"],
+            "M_range_tree_problems": ([int(lay["M"][tree].min()), int(lay["M"][tree].max())]
+                                      if tree.any() else None),
+            "depth_range_tree_problems": ([int(lay["depth"][tree].min()),
+                                           int(lay["depth"][tree].max())] if tree.any() else None)}
 
 
 def _curve(hist, every=5):

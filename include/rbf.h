@@ -455,6 +455,41 @@ RBF_API int rbf_kernel_error(rbf_kernel kernel, double eps, int d, const rbf_fmm
 RBF_API int rbf_autotune(rbf_kernel kernel, double eps, int d, int64_t N, double side, double tol,
                          rbf_fmm_params *params_out, int *depth_out, double *err_out);
 
+/* Unit costs of the FP32 products on the current GPU, in seconds, measured by
+ * rbf_cost_calibrate: a pair of the batched direct sum (4 right-hand sides per
+ * pair), a near-field pair of the FMM, a (point, mode) of P2M + L2P, a (leaf,
+ * mode) of M2M + M2L (both per right-hand side), and what one FMM column costs
+ * beyond its passes inside a CUDA graph (gathers, scatters, launch gaps). */
+typedef struct {
+    double direct_pair_s;
+    double near_pair_s;
+    double point_mode_s;
+    double leaf_mode_s;
+    double column_fixed_s;
+} rbf_cost_model;
+
+/* Measure the cost model on synthetic problems (64 direct sums of 8192 3-D
+ * points; one 3-D FMM product of 65,536 points, M = 12, 4 columns, its passes
+ * timed by CUDA events and its graph replay timed whole).  The result is also
+ * kept as the current device's model for rbf_batch_create.  Synchronises;
+ * allocates about 60 MB while it runs.  Takes a fraction of a second. */
+RBF_API int rbf_cost_calibrate(rbf_cost_model *model_out, void *stream);
+
+/* The cheapest way to apply A to nrhs columns of one problem under the cost
+ * model, among: the direct sum of Eq. (1) (d <= 4; exact; *depth_out = 0,
+ * params M = 0), the near field alone (M = 0, where |Phi| <= tol beyond one
+ * leaf, Eq. (38) without its far part) at the autotuner's depth D or D - 1,
+ * and the FMM with the autotuner's expansion order at D or D - 1 (the order is
+ * searched only when the FMM's cheapest order, M = 8, could beat the best
+ * candidate so far).  Near pairs and occupied leaves are estimated for
+ * uniform points.  *err_out (may be NULL) gets the far-kernel error of the
+ * choice (0 for the direct sum); *pred_s_out (may be NULL) its predicted
+ * seconds per product. */
+RBF_API int rbf_autotune_cost(rbf_kernel kernel, double eps, int d, int64_t N, int nrhs,
+                              double side, double tol, const rbf_cost_model *model,
+                              rbf_fmm_params *params_out, int *depth_out, double *err_out,
+                              double *pred_s_out);
+
 /* One problem of a batch: centres X (device [N][d] FP64, in [0,1]^d), kernel,
  * shape parameter, and the number of right-hand sides. */
 typedef struct {
@@ -468,30 +503,67 @@ typedef struct {
 
 typedef struct rbf_batch rbf_batch;
 
-/* Autotune (tol_kernel) and build a tree for every problem (root [0,1]^d).
- * Vectors of a batch are packed: problem p's right-hand side r occupies
- * [off[p] + r N_p, off[p] + (r+1) N_p) of a device array of `total` doubles
- * (rbf_batch_layout).  The problem array may be freed after the call; the
- * centres must stay alive. */
+/* How rbf_batch_create_opts picks each problem's product. */
+#define RBF_BATCH_AUTO 0   /* rbf_autotune_cost: direct sum, near field alone or FMM */
+#define RBF_BATCH_FMM 1    /* rbf_autotune for every problem (a tree each) */
+#define RBF_BATCH_DIRECT 2 /* the direct sum for every problem with d <= 4 */
+typedef struct {
+    double tol_kernel;            /* far-kernel tolerance of the autotuner (> 0) */
+    int choice;                   /* RBF_BATCH_* */
+    const rbf_cost_model *model;  /* NULL: the current device's model, measured on first use */
+} rbf_batch_opts;
+
+/* Statistics of a batch: problems by product kind, the direct sum's work items,
+ * kernel nodes of the product graph and of the GMRES step graph (0 until
+ * built), wall time of the creation (autotuning, trees, coordinate records),
+ * and the cost model's predicted milliseconds of one batch product. */
+typedef struct {
+    int n_direct, n_near_only, n_fmm;
+    int direct_items;
+    int product_nodes, step_nodes;
+    double setup_s;
+    double predicted_ms;
+    rbf_cost_model model;
+} rbf_batch_stats;
+
+/* Choose every problem's product (opts->choice) and build what it needs: a
+ * tree (root [0,1]^d) for FMM and near-field problems, 16-byte coordinate
+ * records and a work list for the direct sums.  Vectors of a batch are packed:
+ * problem p's right-hand side r occupies [off[p] + r N_p, off[p] + (r+1) N_p)
+ * of a device array of `total` doubles (rbf_batch_layout).  The problem array
+ * may be freed after the call; the centres must stay alive.  Synchronises. */
+RBF_API int rbf_batch_create_opts(const rbf_problem *problems_host, int n_problems,
+                                  const rbf_batch_opts *opts, void *stream, rbf_batch **out);
+/* rbf_batch_create_opts with choice RBF_BATCH_AUTO and the device's model. */
 RBF_API int rbf_batch_create(const rbf_problem *problems_host, int n_problems, double tol_kernel,
                              void *stream, rbf_batch **out);
-/* Host arrays of n_problems entries (any may be NULL). */
+/* Host arrays of n_problems entries (any may be NULL); depth 0 and M 0 mark a
+ * problem summed directly (one leaf holding every centre: all pairs are near). */
 RBF_API int rbf_batch_layout(const rbf_batch *b, int64_t *off_host, int *depth_host, int *M_host,
                              int64_t *total_host);
+RBF_API int rbf_batch_get_stats(const rbf_batch *b, rbf_batch_stats *stats_out);
 /* u = A lambda for every problem and right-hand side (packed device arrays).
  * The first call per precision runs the products once (allocating plans) and
- * captures them into one CUDA graph over several streams; every later call is
- * a copy into the batch's own buffer, one graph launch and a copy out.
+ * captures them into one CUDA graph: the direct sums as one persistent launch
+ * on `stream`, the other problems' products over several streams; every later
+ * call is a copy into the batch's own buffer, one graph launch and a copy out.
  * Asynchronous after the first call. */
 RBF_API int rbf_batch_matvec(rbf_batch *b, rbf_precision prec, const double *lambda_packed,
                              double *u_packed, void *stream);
-/* Restarted GMRES(m) on every system (problem, right-hand side) in lockstep:
- * one graph launch of all products per step, batched CGS2 reductions on the
- * device, Hessenberg problems on the host.  u_packed, lambda_packed: device
- * arrays laid out like the batch buffers (lambda holds the initial guess).
+/* Restarted GMRES(m) on every system (problem, right-hand side) in lockstep,
+ * entirely on the device: one CUDA graph launch per step holds all products,
+ * the two classical Gram-Schmidt passes (batched dot products and updates),
+ * the norm, every system's Givens rotations and least-squares residual, and
+ * v_{j+1}; the column index j lives in device memory, so one graph serves
+ * every step.  A second graph per restart solves the triangular systems,
+ * updates lambda and recomputes the true residual.  The host reads one flag
+ * (any system active) per step.  u_packed, lambda_packed: device arrays laid
+ * out like the batch buffers (lambda holds the initial guess).
  * rel_resid_host[n_systems] (may be NULL) gets ||u - A lambda|| / ||u|| per
- * system for the product in `prec`; *step_ms_host the mean wall time of a
- * GMRES step.  No iterative refinement in batch mode.  Synchronises. */
+ * system for the product in `prec` (the residual of the last restart);
+ * *step_ms_host the mean device time of a step (CUDA events around each step
+ * graph).  No iterative refinement in batch mode.  Allocates (m + 1) packed
+ * vectors; synchronises. */
 RBF_API int rbf_batch_solve(rbf_batch *b, const double *u_packed, double *lambda_packed,
                             int restart_m, int max_iters, double rtol, rbf_precision prec,
                             double *rel_resid_host, int *iters_host, double *step_ms_host,

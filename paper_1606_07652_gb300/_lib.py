@@ -57,6 +57,27 @@ class Problem(ctypes.Structure):
                 ("nrhs", _c_int)]
 
 
+class CostModel(ctypes.Structure):
+    _fields_ = [("direct_pair_s", _c_dbl), ("near_pair_s", _c_dbl), ("point_mode_s", _c_dbl),
+                ("leaf_mode_s", _c_dbl), ("column_fixed_s", _c_dbl)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("tol_kernel", _c_dbl), ("choice", _c_int), ("model", ctypes.POINTER(CostModel))]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("n_direct", _c_int), ("n_near_only", _c_int), ("n_fmm", _c_int),
+                ("direct_items", _c_int), ("product_nodes", _c_int), ("step_nodes", _c_int),
+                ("setup_s", _c_dbl), ("predicted_ms", _c_dbl), ("model", CostModel)]
+
+
+BATCH_AUTO, BATCH_FMM, BATCH_DIRECT = 0, 1, 2
+
+
 class TrainOpts(ctypes.Structure):
     _fields_ = [("n_train", _c_int), ("epochs", _c_int), ("batch", _c_int), ("lr", ctypes.c_float),
                 ("delta_rel", _c_dbl)]
@@ -134,6 +155,11 @@ def load():
     lib.rbf_autotune.argtypes = [_c_int, _c_dbl, _c_int, _c_i64, _c_dbl, _c_dbl, P(FmmParams),
                                  P(_c_int), P(_c_dbl)]
     lib.rbf_batch_create.argtypes = [_c_vp, _c_int, _c_dbl, _c_vp, P(_c_vp)]
+    lib.rbf_batch_create_opts.argtypes = [_c_vp, _c_int, P(BatchOpts), _c_vp, P(_c_vp)]
+    lib.rbf_batch_get_stats.argtypes = [_c_vp, P(BatchStats)]
+    lib.rbf_cost_calibrate.argtypes = [P(CostModel), _c_vp]
+    lib.rbf_autotune_cost.argtypes = [_c_int, _c_dbl, _c_int, _c_i64, _c_int, _c_dbl, _c_dbl,
+                                      P(CostModel), P(FmmParams), P(_c_int), P(_c_dbl), P(_c_dbl)]
     lib.rbf_batch_layout.argtypes = [_c_vp, _c_vp, _c_vp, _c_vp, P(_c_i64)]
     lib.rbf_batch_matvec.argtypes = [_c_vp, _c_int, _c_vp, _c_vp, _c_vp]
     lib.rbf_batch_solve.argtypes = [_c_vp, _c_vp, _c_vp, _c_int, _c_int, _c_dbl, _c_int, _c_vp,
@@ -656,11 +682,33 @@ def autotune(kernel, eps, d, N, tol, side=1.0) -> dict:
             "err": e.value}
 
 
+def cost_calibrate() -> CostModel:
+    """rbf_cost_calibrate: the FP32 unit costs of this GPU (seconds)."""
+    c = CostModel()
+    _check(load().rbf_cost_calibrate(ctypes.byref(c), _stream()), "rbf_cost_calibrate")
+    return c
+
+
+def autotune_cost(kernel, eps, d, N, nrhs, tol, model: CostModel, side=1.0) -> dict:
+    """rbf_autotune_cost: depth 0 means the direct sum."""
+    p = FmmParams()
+    D = _c_int(0)
+    e = _c_dbl(0)
+    t = _c_dbl(0)
+    _check(load().rbf_autotune_cost(kernel, float(eps), d, int(N), int(nrhs), float(side),
+                                    float(tol), ctypes.byref(model), ctypes.byref(p),
+                                    ctypes.byref(D), ctypes.byref(e), ctypes.byref(t)),
+           "rbf_autotune_cost")
+    return {"M": p.M, "period_L": p.period_L, "window_alpha": p.window_alpha, "depth": D.value,
+            "err": e.value, "pred_s": t.value}
+
+
 class Batch:
     """Owner of an rbf_batch: problems = list of dicts(X=CUDA float64 tensor (N, d), kernel,
-    eps, nrhs).  The tensors must outlive the batch."""
+    eps, nrhs).  The tensors must outlive the batch.  choice: BATCH_AUTO (cost model),
+    BATCH_FMM (a tree and autotuned FMM for every problem) or BATCH_DIRECT."""
 
-    def __init__(self, problems, tol_kernel=1e-6):
+    def __init__(self, problems, tol_kernel=1e-6, choice=BATCH_AUTO, model=None):
         arr = (Problem * len(problems))()
         self._keep = []
         for i, q in enumerate(problems):
@@ -669,8 +717,11 @@ class Batch:
             arr[i] = Problem(_dev(X, "float64", "X"), X.shape[0], X.shape[1], q["kernel"],
                              float(q["eps"]), int(q.get("nrhs", 1)))
         h = ctypes.c_void_p()
-        _check(load().rbf_batch_create(arr, len(problems), float(tol_kernel), _stream(),
-                                       ctypes.byref(h)), "rbf_batch_create")
+        self._model = model
+        opts = BatchOpts(float(tol_kernel), int(choice),
+                         ctypes.pointer(model) if model is not None else None)
+        _check(load().rbf_batch_create_opts(arr, len(problems), ctypes.byref(opts), _stream(),
+                                            ctypes.byref(h)), "rbf_batch_create")
         self._h = h
         self.n = len(problems)
         self.problems = problems
@@ -683,6 +734,13 @@ class Batch:
         _check(load().rbf_batch_layout(self._h, _np_ptr(off), _np_ptr(dep), _np_ptr(Ms),
                                        ctypes.byref(tot)), "rbf_batch_layout")
         return {"off": off, "depth": dep, "M": Ms, "total": tot.value}
+
+    def stats(self) -> dict:
+        st = BatchStats()
+        _check(load().rbf_batch_get_stats(self._h, ctypes.byref(st)), "rbf_batch_get_stats")
+        out = {k: getattr(st, k) for k, _ in BatchStats._fields_ if k != "model"}
+        out["model"] = st.model.as_dict()
+        return out
 
     def _packed(self, *named):
         tot = self.layout()["total"]

@@ -37,30 +37,6 @@ struct Src4<double> {
     using type = double4_32a;
 };
 
-// Phi in the product's arithmetic, the kernel fixed at compile time:
-// exp(-(eps r)^2), 1/sqrt(1 + (eps r)^2), sqrt(1 + (eps r)^2) or
-// (1 - eps r)_+^3 (3 eps r + 1).
-template <int KER>
-__device__ __forceinline__ float phi_r2(float e2, float r2)
-{
-    if (KER == RBF_GAUSSIAN) return exp2f(-e2 * r2);  // e2 holds eps^2 * log2(e)
-    if (KER == RBF_IMQ) return rsqrtf(fmaf(e2, r2, 1.0f));
-    if (KER == RBF_MQ) return sqrtf(fmaf(e2, r2, 1.0f));
-    const float q = sqrtf(e2 * r2);
-    const float t = fmaxf(1.0f - q, 0.0f);
-    return t * t * t * fmaf(3.0f, q, 1.0f);
-}
-template <int KER>
-__device__ __forceinline__ double phi_r2(double e2, double r2)
-{
-    if (KER == RBF_GAUSSIAN) return exp(-e2 * r2);
-    if (KER == RBF_IMQ) return rsqrt(fma(e2, r2, 1.0));
-    if (KER == RBF_MQ) return sqrt(fma(e2, r2, 1.0));
-    const double q = sqrt(e2 * r2);
-    const double t = fmax(1.0 - q, 0.0);
-    return t * t * t * fma(3.0, q, 1.0);
-}
-
 // f(std::integral_constant<int, K>) for the run-time kernel id K
 template <typename F>
 int with_kernel(int kernel, F f)

@@ -103,6 +103,30 @@ __host__ __device__ inline double rbf_phi64(int kernel, double e2r2)
     return 1.0 / sqrt(1.0 + e2r2);
 }
 
+// Phi in the product's arithmetic, the kernel fixed at compile time:
+// exp(-(eps r)^2), 1/sqrt(1 + (eps r)^2), sqrt(1 + (eps r)^2) or
+// (1 - eps r)_+^3 (3 eps r + 1).
+template <int KER>
+__device__ __forceinline__ float phi_r2(float e2, float r2)
+{
+    if (KER == RBF_GAUSSIAN) return exp2f(-e2 * r2);  // e2 holds eps^2 * log2(e)
+    if (KER == RBF_IMQ) return rsqrtf(fmaf(e2, r2, 1.0f));
+    if (KER == RBF_MQ) return sqrtf(fmaf(e2, r2, 1.0f));
+    const float q = sqrtf(e2 * r2);
+    const float t = fmaxf(1.0f - q, 0.0f);
+    return t * t * t * fmaf(3.0f, q, 1.0f);
+}
+template <int KER>
+__device__ __forceinline__ double phi_r2(double e2, double r2)
+{
+    if (KER == RBF_GAUSSIAN) return exp(-e2 * r2);
+    if (KER == RBF_IMQ) return rsqrt(fma(e2, r2, 1.0));
+    if (KER == RBF_MQ) return sqrt(fma(e2, r2, 1.0));
+    const double q = sqrt(e2 * r2);
+    const double t = fmax(1.0 - q, 0.0);
+    return t * t * t * fma(3.0, q, 1.0);
+}
+
 __device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
 
@@ -283,5 +307,27 @@ int rbf_matvec_sorted64(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fm
                         int prec, const double *lam_sorted, double *u_sorted, cudaStream_t s);
 
 void rbf_default_params(rbf_kernel kernel, double side, rbf_fmm_params *p);
+
+// ------------------------------------------------- batched direct sums ---
+// The problems of a batch whose plain sum (Eq. (1)) is cheaper than their FMM:
+// one persistent launch over a work list of (problem, column group, target
+// tile) items (batch_direct.cu).
+struct rbf_direct_set {
+    int np = 0;
+    int nitems = 0, nitems64 = 0;  // FP32 items, then FP64 items (half-size tiles)
+    int4 *items = nullptr;
+    int *ctr = nullptr;            // [2] work-queue counters, zeroed before each launch
+    int64_t *N = nullptr, *off = nullptr, *xoff = nullptr;  // per direct problem
+    int *nrhs = nullptr, *ker = nullptr, *dim = nullptr;
+    double *eps = nullptr;
+    double *x64 = nullptr;         // [points][4] coordinates, zero-padded
+    float4 *x32 = nullptr;
+    int grid32 = 0, grid64 = 0;    // resident CTAs
+};
+int rbf_direct_set_build(rbf_direct_set *ds, const rbf_problem *probs, const int64_t *off,
+                         const std::vector<int> &which, cudaStream_t s);
+int rbf_direct_set_run(const rbf_direct_set *ds, int prec, const double *lam, double *u,
+                       cudaStream_t s);
+void rbf_direct_set_free(rbf_direct_set *ds);
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

@@ -1,13 +1,18 @@
-"""Autotuner and batched products/solves on the GPU.
+"""Autotuner, cost model and batched products/solves on the GPU.
 
-The batched product (one CUDA graph over all problems and right-hand sides)
-must give the same bits as the per-problem entry point with the same
-parameters, and match the FP64 oracle FMM within the FP32 bound; the measured
-far-kernel error must reproduce the oracle's calibration."""
+With every problem on the FMM, the batched product (one CUDA graph over all
+problems and right-hand sides) must give the same bits as the per-problem
+entry point with the same parameters, and match the FP64 oracle FMM within the
+FP32 bound.  Problems the cost model sends to the direct sum must match the
+oracle's plain sum of Eq. (1) element by element (FP32 within 5e-6 of max |u|,
+FP64 within 1e-12).  The measured far-kernel error must reproduce the oracle's
+calibration, and the batched GMRES (one graph per step, all on the device)
+must report the residuals an independent product gives."""
 import numpy as np
 import pytest
 
 import oracle as O
+import workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -67,7 +72,7 @@ def _problems(torch, n, seed):
 def test_batch_matvec_packed(env):
     rbf, _lib, torch = env
     probs = _problems(torch, 7, 3)
-    B = _lib.Batch(probs, tol_kernel=1e-5)
+    B = _lib.Batch(probs, tol_kernel=1e-5, choice=_lib.BATCH_FMM)
     lay = B.layout()
     total = lay["total"]
     lam = np.random.default_rng(5).standard_normal(total)
@@ -125,3 +130,201 @@ def test_batch_solve_residuals(env):
             assert abs(res - rep["rel_resid"][s]) <= 1e-6 + 1e-3 * res
             assert res < 1.0
             s += 1
+
+
+def _direct_problems(torch, seed):
+    """d = 1..4, all four kernels, 1..6 right-hand sides (two column groups), sizes
+    from one tile to several with ragged tails."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for k, (N, d, kern, nrhs) in enumerate([(1, 2, O.GAUSSIAN, 1), (37, 1, O.IMQ, 2),
+                                             (513, 2, O.MQ, 3), (1500, 3, O.WENDLAND, 4),
+                                             (2049, 3, O.GAUSSIAN, 6), (700, 4, O.IMQ, 5),
+                                             (4096, 2, O.IMQ, 4)]):
+        eps = 0.5 if kern == O.WENDLAND else float(rng.uniform(1, 5))
+        probs.append(dict(X=torch.as_tensor(rng.random((N, d)), device="cuda"), kernel=kern,
+                          eps=eps, nrhs=nrhs))
+    return probs
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batched_direct_sum_matches_oracle(env, prec):
+    """Every problem through the persistent direct-sum launch: element-wise against the
+    oracle's Eq. (1) at every target of every column."""
+    rbf, _lib, torch = env
+    probs = _direct_problems(torch, 17)
+    B = _lib.Batch(probs, tol_kernel=1e-6, choice=_lib.BATCH_DIRECT)
+    lay = B.layout()
+    st = B.stats()
+    assert st["n_direct"] == len(probs) and st["n_fmm"] == 0 and st["direct_items"] >= len(probs)
+    assert np.all(lay["depth"] == 0) and np.all(lay["M"] == 0)
+    lam = np.random.default_rng(5).standard_normal(lay["total"])
+    P = rbf.FP32 if prec == "fp32" else rbf.FP64
+    u = _batch_product(B, torch, lam, P)
+    again = _batch_product(B, torch, lam, P)
+    assert np.array_equal(u, again)     # deterministic: no atomics on the outputs
+    tol = 5e-6 if prec == "fp32" else 1e-12
+    worst = 0.0
+    for p, q in enumerate(probs):
+        X = q["X"].cpu().numpy()
+        N = X.shape[0]
+        for r in range(q["nrhs"]):
+            a = lay["off"][p] + r * N
+            ref = O.direct(X, lam[a:a + N], q["kernel"], q["eps"])
+            err = np.max(np.abs(u[a:a + N] - ref)) / np.max(np.abs(ref))
+            worst = max(worst, err)
+            assert err <= tol, (p, r, err)
+    print(f"batched direct {prec}: worst element error {worst:.2e} of max |u|")
+    B.free()
+
+
+def test_cost_model_and_choice(env):
+    """The calibrated unit costs are positive; the cost-model autotuner sends a small
+    problem to the direct sum and a large smooth one to the FMM, and its choice is the
+    cheapest of what it predicts."""
+    rbf, _lib, torch = env
+    c = _lib.cost_calibrate()
+    d = c.as_dict()
+    print("cost model:", d)
+    assert all(np.isfinite(v) and v > 0 for v in d.values())
+    small = _lib.autotune_cost(O.IMQ, 2.0, 3, 1000, 4, 1e-6, c)
+    assert small["depth"] == 0 and small["M"] == 0 and small["err"] == 0.0
+    big = _lib.autotune_cost(O.IMQ, 2.0, 3, 1 << 20, 1, 1e-6, c)
+    assert big["depth"] >= 2 and big["M"] > 0 and big["err"] <= 1e-6
+    # the direct sum of 2^20 points would take N^2 pairs
+    assert big["pred_s"] < c.direct_pair_s * float(1 << 20) ** 2
+    narrow = _lib.autotune_cost(O.GAUSSIAN, 60.0, 3, 200000, 1, 1e-6, c)
+    assert narrow["depth"] >= 2 and narrow["M"] == 0     # near field alone
+
+
+def test_auto_batch_mixed_matches_oracle_and_single_products(env):
+    """A batch the cost model splits between the direct sum and trees: direct problems
+    against the oracle's Eq. (1), tree problems bit for bit against the per-problem
+    entry point with the batch's parameters."""
+    rbf, _lib, torch = env
+    rng = np.random.default_rng(23)
+    probs = []
+    for N, d, kern, eps in [(600, 2, O.IMQ, 3.0), (1200, 3, O.GAUSSIAN, 2.0),
+                            (120000, 3, O.GAUSSIAN, 1.0), (90000, 2, O.IMQ, 1.0),
+                            (60000, 3, O.GAUSSIAN, 40.0)]:
+        probs.append(dict(X=torch.as_tensor(rng.random((N, d)), device="cuda"), kernel=kern,
+                          eps=eps, nrhs=2))
+    B = _lib.Batch(probs, tol_kernel=1e-6)
+    lay = B.layout()
+    st = B.stats()
+    print("mixed batch:", st, "depth", lay["depth"], "M", lay["M"])
+    assert st["n_direct"] >= 2 and st["n_direct"] + st["n_near_only"] + st["n_fmm"] == len(probs)
+    assert st["n_near_only"] + st["n_fmm"] >= 1
+    lam = rng.standard_normal(lay["total"])
+    u = _batch_product(B, torch, lam, rbf.FP32)
+    for p, q in enumerate(probs):
+        X = q["X"].cpu().numpy()
+        N, nr = X.shape[0], q["nrhs"]
+        seg = lam[lay["off"][p]:lay["off"][p] + N * nr].reshape(nr, N)
+        got = u[lay["off"][p]:lay["off"][p] + N * nr].reshape(nr, N)
+        if lay["depth"][p] == 0:
+            tg = np.arange(0, N, max(1, N // 500))
+            for r in range(nr):
+                ref = O.direct(X, seg[r], q["kernel"], q["eps"], tg)
+                assert np.max(np.abs(got[r][tg] - ref)) <= 5e-6 * np.max(np.abs(ref))
+        else:
+            prm = _lib.autotune_cost(q["kernel"], q["eps"], X.shape[1], N, nr, 1e-6,
+                                     _lib.CostModel(**st["model"]))
+            assert prm["depth"] == lay["depth"][p] and prm["M"] == lay["M"][p]
+            t = rbf.tree_build(q["X"], lo=np.zeros(X.shape[1]), side=1.0, depth=int(lay["depth"][p]))
+            U = torch.empty((nr, N), dtype=torch.float64, device="cuda")
+            rbf.fmm_matvec(t, q["kernel"], q["eps"], torch.as_tensor(seg, device="cuda"), U,
+                           prec=rbf.FP32, M=prm["M"], period_L=prm["period_L"],
+                           window_alpha=prm["window_alpha"])
+            assert np.array_equal(got, U.cpu().numpy())
+            t.free()
+    B.free()
+
+
+def _jittered_problem(torch, n1, d, seed, kernel, eh, nrhs):
+    X = workloads.jittered_grid(n1, d, seed)
+    return dict(X=torch.as_tensor(X, device="cuda"), kernel=kernel, eps=eh * n1, nrhs=nrhs)
+
+
+def _oracle_its(probs, lay, u, m, rtol):
+    from oracle import solver as OS
+    its = []
+    for p, q in enumerate(probs):
+        X = q["X"].cpu().numpy()
+        N = X.shape[0]
+        for r in range(q["nrhs"]):
+            a = lay["off"][p] + r * N
+            _, it, _ = OS.gmres(lambda x: O.direct(X, x, q["kernel"], q["eps"]), u[a:a + N],
+                                m=m, tol=rtol, maxit=600)
+            its.append(it)
+    return its
+
+
+def test_batch_solve_matches_oracle_gmres(env):
+    """Direct-sum systems solved on the device, FP64.  One system alone follows the
+    oracle's GMRES(m) (same restart length, CGS2, Givens, restart from the true
+    residual) on the oracle's plain sum: same iteration count within 2.  Several
+    systems in lockstep all reach the tolerance; a system whose estimate converges
+    mid-cycle waits for the common restart (the oracle restarts it at once), so the
+    lockstep count is close to, not equal to, the largest single count."""
+    rbf, _lib, torch = env
+    m, rtol = 20, 1e-10
+    rng = np.random.default_rng(8)
+    one = [_jittered_problem(torch, 28, 2, 3, O.IMQ, 1.5, 1)]
+    B = _lib.Batch(one, tol_kernel=1e-9, choice=_lib.BATCH_DIRECT)
+    lay = B.layout()
+    u = rng.standard_normal(lay["total"])
+    lam = torch.zeros(lay["total"], dtype=torch.float64, device="cuda")
+    rep = B.solve(torch.as_tensor(u, device="cuda"), lam, restart_m=m, max_iters=600, rtol=rtol,
+                  prec=rbf.FP64)
+    its = _oracle_its(one, lay, u, m, rtol)
+    print("one system: device", rep["iters"], "oracle", its)
+    assert rep["rel_resid"][0] <= rtol and abs(rep["iters"] - its[0]) <= 2
+    B.free()
+    probs = [_jittered_problem(torch, 20, 2, 1, O.GAUSSIAN, 1.2, 2),
+             _jittered_problem(torch, 8, 3, 2, O.GAUSSIAN, 1.4, 2),
+             _jittered_problem(torch, 28, 2, 3, O.IMQ, 1.5, 1)]
+    B = _lib.Batch(probs, tol_kernel=1e-9, choice=_lib.BATCH_DIRECT)
+    lay = B.layout()
+    u = rng.standard_normal(lay["total"])
+    lam = torch.zeros(lay["total"], dtype=torch.float64, device="cuda")
+    rep = B.solve(torch.as_tensor(u, device="cuda"), lam, restart_m=m, max_iters=600, rtol=rtol,
+                  prec=rbf.FP64)
+    its = _oracle_its(probs, lay, u, m, rtol)
+    print("lockstep steps", rep["iters"], "oracle per system", its, "ms/step", rep["step_ms"])
+    assert np.all(rep["rel_resid"] <= rtol)
+    assert 0.8 * max(its) <= rep["iters"] <= 1.25 * max(its) + 2
+    B.free()
+
+
+def test_batch_solve_on_device_converges(env):
+    """Mixed direct / near-field batch on quasi-uniform centres solved to 1e-8 with
+    GMRES(30) steps as one graph each: every system converges, the reported residuals
+    agree with an independent product, and the step graph was built."""
+    rbf, _lib, torch = env
+    probs = [_jittered_problem(torch, 30, 2, 4, O.GAUSSIAN, 1.3, 2),
+             _jittered_problem(torch, 12, 3, 5, O.GAUSSIAN, 1.2, 2),
+             _jittered_problem(torch, 24, 3, 6, O.GAUSSIAN, 1.6, 2)]
+    B = _lib.Batch(probs, tol_kernel=1e-9)
+    lay = B.layout()
+    st = B.stats()
+    assert st["n_direct"] >= 1 and st["n_near_only"] + st["n_fmm"] >= 1, (st, lay)
+    rng = np.random.default_rng(41)
+    u = torch.as_tensor(rng.standard_normal(lay["total"]), device="cuda")
+    lam = torch.zeros_like(u)
+    rep = B.solve(u, lam, restart_m=30, max_iters=400, rtol=1e-8, prec=rbf.FP64)
+    st = B.stats()
+    print("solve:", rep["iters"], "steps", rep["step_ms"], "ms/step", st)
+    assert st["step_nodes"] > 0
+    assert np.all(rep["rel_resid"] <= 1e-8), rep["rel_resid"]
+    Au = _batch_product(B, torch, lam.cpu().numpy(), rbf.FP64)
+    un = u.cpu().numpy()
+    s = 0
+    for p, q in enumerate(probs):
+        N = q["X"].shape[0]
+        for r in range(q["nrhs"]):
+            a = lay["off"][p] + r * N
+            res = np.linalg.norm(un[a:a + N] - Au[a:a + N]) / np.linalg.norm(un[a:a + N])
+            assert res <= 1.5e-8 and abs(res - rep["rel_resid"][s]) <= 1e-10 + 1e-3 * res
+            s += 1
+    B.free()
