@@ -84,6 +84,14 @@
 // once per chunk; 0 = warp shuffles per point
 // FP32 3-D grouped coupling: modes per thread (1 or 2; two need 141 registers and ran
 // slower, 3.53 against 3.42 ms at the 3-D M = 32 product)
+#ifndef RBF_M2L_MINB
+#define RBF_M2L_MINB 8                 // resident CTAs of 128 threads: 64 registers, no spills
+#endif
+#if RBF_M2L_MINB > 0
+#define RBF_M2L_BOUNDS __launch_bounds__(128, RBF_M2L_MINB)
+#else
+#define RBF_M2L_BOUNDS __launch_bounds__(128)
+#endif
 #ifndef RBF_M2L_MP
 #define RBF_M2L_MP 1
 #endif
@@ -497,6 +505,13 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? far_bmax(DENSE, NCE) : 256,
 constexpr int kHorner = 8;       // columns per Horner group (the last takes up to 7 more)
 constexpr int kHornerMaxCol = 33;
 constexpr int kHornerBlock = 192;  // 96 registers: three CTAs of six warps per SM
+#ifndef RBF_L2P_SPLIT
+#define RBF_L2P_SPLIT 1              // half a row per thread for rows of two groups or more
+#endif
+#ifndef RBF_L2P_BLOCK2
+#define RBF_L2P_BLOCK2 256
+#endif
+constexpr int kHornerBlock2 = RBF_L2P_BLOCK2;
 constexpr int kHornerPch = 64;     // points per table chunk
 
 __device__ __forceinline__ float2 horner_step(float2 h, float2 z, float2 l)
@@ -509,9 +524,17 @@ __device__ __forceinline__ float2 horner_step(float2 h, float2 z, float2 l)
     return r;
 }
 
+// groups of a row of NC columns: 8 columns each, the last one takes the rest
+__host__ __device__ constexpr int horner_ng(int NC) { return NC >= kHorner ? NC / kHorner : 1; }
+// columns held by a thread that takes groups GB .. GE-1 (from column 8 GB on)
+__host__ __device__ constexpr int horner_held(int NC, int GB, int GE)
+{
+    return (GE >= horner_ng(NC) ? NC : kHorner * GE) - kHorner * GB;
+}
+
 // S_k (+)= ph_k * sum_{q<LEN} L[B+q] z_k^q for two points k
-template <int NC, int LEN, int B, bool FIRST>
-__device__ __forceinline__ void horner_group2(const float2 (&L)[NC], const float2 (&z)[2],
+template <int NL, int LEN, int B, bool FIRST>
+__device__ __forceinline__ void horner_group2(const float2 (&L)[NL], const float2 (&z)[2],
                                               const float2 (&ph)[2], float2 (&S)[2])
 {
     float2 h[2];
@@ -528,18 +551,19 @@ __device__ __forceinline__ void horner_group2(const float2 (&L)[NC], const float
     }
 }
 
-// all groups of a row; group g starts at column 8 g, its phase is rec[1 + g]
-template <int NC, int G>
-__device__ __forceinline__ void horner_groups(const float2 (&L)[NC], const float2 *ra,
-                                              const float2 *rb, const float2 (&z)[2],
-                                              float2 (&S)[2])
+// groups G .. GE-1 of a row whose held columns start at group GB; group g starts
+// at column 8 g and its phase is rec[1 + g]
+template <int NC, int GB, int GE, int G>
+__device__ __forceinline__ void horner_groups(const float2 (&L)[horner_held(NC, GB, GE)],
+                                              const float2 *ra, const float2 *rb,
+                                              const float2 (&z)[2], float2 (&S)[2])
 {
-    constexpr int NG = NC >= kHorner ? NC / kHorner : 1;
+    constexpr int NG = horner_ng(NC);
     constexpr int LEN = NC < kHorner ? NC : (G + 1 < NG ? kHorner : NC - kHorner * G);
-    if constexpr (G < NG) {
+    if constexpr (G < GE) {
         const float2 ph[2] = {ra[1 + G], rb[1 + G]};
-        horner_group2<NC, LEN, kHorner * G, G == 0>(L, z, ph, S);
-        horner_groups<NC, G + 1>(L, ra, rb, z, S);
+        horner_group2<horner_held(NC, GB, GE), LEN, kHorner * (G - GB), G == GB>(L, z, ph, S);
+        horner_groups<NC, GB, GE, G + 1>(L, ra, rb, z, S);
     }
 }
 
@@ -554,25 +578,29 @@ __device__ __forceinline__ float row_part(const float2 *Ep, int d, const RowOff 
     return A.x * S.x - A.y * S.y;
 }
 
-template <int NC, bool D3>
+// the rows roff + lane, roff + lane + rstride, ... of the leaf, groups GB .. GE-1
+// of each (a thread holds those columns of its row in registers); every point's
+// contribution is reduced over the warp's 32 rows and added to the warp's slot
+template <int NC, int GB, int GE, bool D3>
 __device__ __forceinline__ void horner_rows(const FarArgs<float> &a, const float2 *E, int rowlen,
-                                            int rflen, int cnt, float *part)
+                                            int rflen, int cnt, float *part, int roff, int rstride)
 {
     using C = float2;
+    constexpr int NL = horner_held(NC, GB, GE);
     const int d = a.d, nrow = a.nrow;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool hi16 = lane >= 16, hi8 = (lane & 8) != 0;
     const C *Lleaf = a.Lx + (int64_t)blockIdx.x * a.mstride;
     float *wpart = part + warp * a.pch;
-    for (int row0 = 0; row0 < nrow; row0 += blockDim.x) {
-        if (row0 + warp * 32 >= nrow) break;  // the whole warp is past the last row
-        const int row = row0 + threadIdx.x;
+    for (int row0 = 0; row0 < nrow; row0 += rstride) {
+        if (row0 + roff >= nrow) break;  // the whole warp is past the last row
+        const int row = row0 + roff + lane;
         const bool act = row < nrow;
-        C L[NC];
-        const C *lrow = Lleaf + (int64_t)(act ? row : 0) * a.ncol;
+        C L[NL];
+        const C *lrow = Lleaf + (int64_t)(act ? row : 0) * a.ncol + kHorner * GB;
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-            if (act && q < a.ncol) L[q] = lrow[q];
+        for (int q = 0; q < NL; ++q) {
+            if (act && kHorner * GB + q < a.ncol) L[q] = lrow[q];
             else L[q].x = L[q].y = 0.f;
         }
         const RowOff ro = row_offsets(act ? row : 0, d, a.n1, a.seg0, a.seg);
@@ -584,7 +612,7 @@ __device__ __forceinline__ void horner_rows(const FarArgs<float> &a, const float
                 const C *Ea = E + pa * rowlen, *Eb = E + pb * rowlen;
                 const C z[2] = {Ea[rflen], Eb[rflen]};
                 C S[2];
-                horner_groups<NC, 0>(L, Ea + rflen, Eb + rflen, z, S);
+                horner_groups<NC, GB, GE, GB>(L, Ea + rflen, Eb + rflen, z, S);
                 const float va = row_part<D3>(Ea, d, ro, S[0]);
                 const float vb = row_part<D3>(Eb, d, ro, S[1]);
                 v[2 * h] = act && p + 2 * h < cnt ? va : 0.f;
@@ -606,11 +634,11 @@ __device__ __forceinline__ void horner_rows(const FarArgs<float> &a, const float
     }
 }
 
-template <int NC>
-__global__ void __maxnreg__(96) k_l2p_horner(FarArgs<float> a, int reclen)
+template <int NC, bool SPLIT>
+__device__ __forceinline__ void l2p_horner_body(const FarArgs<float> &a, int reclen)
 {
     using C = float2;
-    constexpr int NG = NC >= kHorner ? NC / kHorner : 1;
+    constexpr int NG = horner_ng(NC);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int d = a.d, seg0 = a.seg0, seg = a.seg;
     const int rflen = d == 1 ? 0 : seg0 + (d - 2) * seg;  // row-factor tables (dims 0..d-2)
@@ -664,8 +692,24 @@ __global__ void __maxnreg__(96) k_l2p_horner(FarArgs<float> a, int reclen)
         }
         for (int q = threadIdx.x; q < nwarp * a.pch; q += blockDim.x) part[q] = 0.f;
         __syncthreads();
-        if (d == 3) horner_rows<NC, true>(a, E, rowlen, rflen, cnt, part);
-        else horner_rows<NC, false>(a, E, rowlen, rflen, cnt, part);
+        if constexpr (!SPLIT) {
+            const int roff = (threadIdx.x >> 5) * 32, rstride = blockDim.x;
+            if (d == 3) horner_rows<NC, 0, NG, true>(a, E, rowlen, rflen, cnt, part, roff, rstride);
+            else horner_rows<NC, 0, NG, false>(a, E, rowlen, rflen, cnt, part, roff, rstride);
+        } else {
+            // warp pairs share 32 rows: the even warp takes the first half of the
+            // groups, the odd warp the rest (each holds half a row in registers)
+            constexpr int GM = NG / 2;
+            const int warp = threadIdx.x >> 5;
+            const int roff = (warp >> 1) * 32, rstride = (nwarp >> 1) * 32;
+            if ((warp & 1) == 0) {
+                if (d == 3) horner_rows<NC, 0, GM, true>(a, E, rowlen, rflen, cnt, part, roff, rstride);
+                else horner_rows<NC, 0, GM, false>(a, E, rowlen, rflen, cnt, part, roff, rstride);
+            } else {
+                if (d == 3) horner_rows<NC, GM, NG, true>(a, E, rowlen, rflen, cnt, part, roff, rstride);
+                else horner_rows<NC, GM, NG, false>(a, E, rowlen, rflen, cnt, part, roff, rstride);
+            }
+        }
         __syncthreads();
         for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
             float sum = 0.f;
@@ -673,6 +717,22 @@ __global__ void __maxnreg__(96) k_l2p_horner(FarArgs<float> a, int reclen)
             a.u[p0 + ch0 + p] = sum;
         }
     }
+}
+
+template <int NC>
+__global__ void __maxnreg__(96) k_l2p_horner(FarArgs<float> a, int reclen)
+{
+    l2p_horner_body<NC, false>(a, reclen);
+}
+
+#ifndef RBF_L2P_SPLIT_REGS
+#define RBF_L2P_SPLIT_REGS 64
+#endif
+// rows of at least two groups: half a row per thread, so twice the warps fit
+template <int NC>
+__global__ void __maxnreg__(RBF_L2P_SPLIT_REGS) k_l2p_horner2(FarArgs<float> a, int reclen)
+{
+    l2p_horner_body<NC, true>(a, reclen);
 }
 
 // ------------------------------------------------------------------ M2M ---
@@ -886,7 +946,7 @@ __global__ void k_m2l(int d, int M, int D, int n1, int64_t nmode, int64_t ms, co
 // is summed one dimension at a time over the block, so each neighbour
 // expansion is read once per CTA instead of once per target.
 template <typename R, int DIM, int MP>
-__global__ void __launch_bounds__(128) k_m2l_grp(int M, int D, int n1, int nmode, int64_t ms,
+__global__ void RBF_M2L_BOUNDS k_m2l_grp(int M, int D, int n1, int nmode, int64_t ms,
                                                  const cplx<R> *shD,
                                                  const R *omegaC, const cplx<R> *root_ph,
                                                  const uint64_t *parent_key, const int32_t *nb4,
@@ -1429,19 +1489,28 @@ namespace {
 template <int NC>
 int launch_l2p_horner(const FarArgs<float> &a0, int nleaf, cudaStream_t s)
 {
-    constexpr int NG = NC >= kHorner ? NC / kHorner : 1;
+    constexpr int NG = horner_ng(NC);
+    constexpr bool split = RBF_L2P_SPLIT && NG >= 2;
     FarArgs<float> a = a0;
     a.seg0 = a.d == 1 ? 0 : even_up(a.n0);
     a.seg = even_up(a.n1);
     const int reclen = even_up(NG + 1);
     const int rflen = a.d == 1 ? 0 : a.seg0 + (a.d - 2) * a.seg;
     const int rowlen = rflen + reclen;
-    const int bd = std::min(kHornerBlock, 32 * ((a.nrow + 31) / 32));
+    // split: an even number of warps, 32 rows per warp pair
+    const int bd = split ? std::min(kHornerBlock2, 64 * ((a.nrow + 31) / 32))
+                         : std::min(kHornerBlock, 32 * ((a.nrow + 31) / 32));
     a.pch = kHornerPch;
     const size_t smem = (size_t)a.pch * (rowlen * sizeof(float2) + (bd / 32) * sizeof(float));
-    RBF_CUDA_TRY(cudaFuncSetAttribute(k_l2p_horner<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    k_l2p_horner<NC><<<nleaf, bd, smem, s>>>(a, reclen);
+    if constexpr (split) {
+        RBF_CUDA_TRY(cudaFuncSetAttribute(k_l2p_horner2<NC>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_l2p_horner2<NC><<<nleaf, bd, smem, s>>>(a, reclen);
+    } else {
+        RBF_CUDA_TRY(cudaFuncSetAttribute(k_l2p_horner<NC>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_l2p_horner<NC><<<nleaf, bd, smem, s>>>(a, reclen);
+    }
     RBF_LAUNCH_CHECK();
     return RBF_OK;
 }

@@ -22,6 +22,9 @@ constexpr int P2P_STAGE_BYTES = 16384;         // shared memory for staged sourc
 #ifndef RBF_P2P_TGMAX
 #define RBF_P2P_TGMAX 4                        // target groups of 32 per pass, at most
 #endif
+#ifndef RBF_P2P_TT
+#define RBF_P2P_TT 2                           // targets per thread of the split kernel
+#endif
 #ifndef RBF_P2P_SMALL
 #define RBF_P2P_SMALL 64                       // leaves up to this size: one group per pass
 #endif
@@ -226,15 +229,17 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(R e2, int64_t N, const R *x
     }
 }
 
-// Leaves of at most P2P_THREADS points: the CTA's threads are (target, source
-// split) pairs, nsplit = floor(P2P_THREADS / nt) splits of the staged sources,
-// so that nearly every lane works whatever the leaf size and the sources are
-// staged once.  Thread tid takes target tid % nt and split tid / nt; the lanes
-// of a warp mostly share a split and so read the same staged source (one
-// broadcast).  Split k takes the sources j = k, k + nsplit, ... of each chunk,
-// SU at a time with independent partial sums; the partial sums of a target
-// are added over the splits in a fixed order.
-template <typename R, int DIM, int KER>
+// Leaves of at most P2P_THREADS points: the CTA's threads are (target group,
+// source split) pairs.  A group holds TT targets (g, g + ng, ... with ng =
+// ceil(nt / TT) groups), so every staged source read feeds TT pair evaluations;
+// nsplit = floor(P2P_THREADS / ng) splits of the staged sources, so that nearly
+// every lane works whatever the leaf size and the sources are staged once.
+// Thread tid takes group tid % ng and split tid / ng; the lanes of a warp
+// mostly share a split and so read the same staged source (one broadcast).
+// Split k takes the sources j = k, k + nsplit, ... of each chunk, SU at a time
+// with independent partial sums; the partial sums of a target are added over
+// the splits in a fixed order.
+template <typename R, int DIM, int KER, int TT>
 __global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, const R *xs,
                                                            const R *lam, const int32_t *leaf_off,
                                                            const int32_t *near_off,
@@ -246,21 +251,28 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, cons
     constexpr int SU = RBF_P2P_SU;
     __shared__ S4 src[P2P_SCHUNK * REC];
     __shared__ int32_t rstart[729], rpre[730];
-    __shared__ R red[P2P_THREADS];
+    __shared__ R red[TT][P2P_THREADS];
     const int a = blockIdx.x;
     const int e0 = near_off[a], ne = near_off[a + 1] - e0;
     near_ranges(e0, ne, near_idx, leaf_off, rstart, nullptr, rpre);
     const int nsrc = rpre[ne];
     const int t0 = leaf_off[a], nt = leaf_off[a + 1] - t0;  // 1 <= nt <= P2P_THREADS
-    const int nsplit = P2P_THREADS / nt;
-    const int tgt = threadIdx.x % nt, sp = threadIdx.x / nt;
+    const int ng = (nt + TT - 1) / TT;
+    const int nsplit = P2P_THREADS / ng;
+    const int grp = threadIdx.x % ng, sp = threadIdx.x / ng;
     const bool active = sp < nsplit;
-    R xt[DIM];
+    R xt[TT][DIM];
 #pragma unroll
-    for (int t = 0; t < DIM; ++t) xt[t] = xs[(int64_t)t * N + t0 + tgt];
-    R acc[SU];
+    for (int q = 0; q < TT; ++q) {
+        const int tq = min(grp + q * ng, nt - 1);
 #pragma unroll
-    for (int k = 0; k < SU; ++k) acc[k] = (R)0;
+        for (int t = 0; t < DIM; ++t) xt[q][t] = xs[(int64_t)t * N + t0 + tq];
+    }
+    R acc[TT][SU];
+#pragma unroll
+    for (int q = 0; q < TT; ++q)
+#pragma unroll
+        for (int k = 0; k < SU; ++k) acc[q][k] = (R)0;
     for (int s0 = 0; s0 < nsrc; s0 += P2P_SCHUNK) {
         const int cnt = min(P2P_SCHUNK, nsrc - s0);
         __syncthreads();
@@ -304,43 +316,50 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, cons
                 S4 r1;
                 if (REC == 2) r1 = src[REC * j + 1];
                 const R wgt = !masked || jj < cnt ? r0.w : (R)0;
-                R d0 = xt[0] - r0.x;
-                R r2 = d0 * d0;
-                if (DIM > 1) {
-                    R d1 = xt[DIM > 1 ? 1 : 0] - r0.y;
-                    r2 = fma(d1, d1, r2);
+#pragma unroll
+                for (int q = 0; q < TT; ++q) {
+                    R d0 = xt[q][0] - r0.x;
+                    R r2 = d0 * d0;
+                    if (DIM > 1) {
+                        R d1 = xt[q][DIM > 1 ? 1 : 0] - r0.y;
+                        r2 = fma(d1, d1, r2);
+                    }
+                    if (DIM > 2) {
+                        R d2 = xt[q][DIM > 2 ? 2 : 0] - r0.z;
+                        r2 = fma(d2, d2, r2);
+                    }
+                    if (DIM > 3) {
+                        R d3 = xt[q][DIM > 3 ? 3 : 0] - r1.x;
+                        r2 = fma(d3, d3, r2);
+                    }
+                    if (DIM > 4) {
+                        R d4 = xt[q][DIM > 4 ? 4 : 0] - r1.y;
+                        r2 = fma(d4, d4, r2);
+                    }
+                    if (DIM > 5) {
+                        R d5 = xt[q][DIM > 5 ? 5 : 0] - r1.z;
+                        r2 = fma(d5, d5, r2);
+                    }
+                    acc[q][k] = fma(wgt, phi_r2<KER>(e2, r2), acc[q][k]);
                 }
-                if (DIM > 2) {
-                    R d2 = xt[DIM > 2 ? 2 : 0] - r0.z;
-                    r2 = fma(d2, d2, r2);
-                }
-                if (DIM > 3) {
-                    R d3 = xt[DIM > 3 ? 3 : 0] - r1.x;
-                    r2 = fma(d3, d3, r2);
-                }
-                if (DIM > 4) {
-                    R d4 = xt[DIM > 4 ? 4 : 0] - r1.y;
-                    r2 = fma(d4, d4, r2);
-                }
-                if (DIM > 5) {
-                    R d5 = xt[DIM > 5 ? 5 : 0] - r1.z;
-                    r2 = fma(d5, d5, r2);
-                }
-                acc[k] = fma(wgt, phi_r2<KER>(e2, r2), acc[k]);
             }
         };
         int j0 = sp;
         for (; j0 + (SU - 1) * nsplit < cnt; j0 += SU * nsplit) step(j0, false);
         if (j0 < cnt) step(j0, true);
     }
-    R tsum = acc[0];
 #pragma unroll
-    for (int k = 1; k < SU; ++k) tsum += acc[k];
-    red[threadIdx.x] = active ? tsum : (R)0;
+    for (int q = 0; q < TT; ++q) {
+        R tsum = acc[q][0];
+#pragma unroll
+        for (int k = 1; k < SU; ++k) tsum += acc[q][k];
+        red[q][threadIdx.x] = active ? tsum : (R)0;
+    }
     __syncthreads();
     if (threadIdx.x < nt) {
-        R sum = red[threadIdx.x];
-        for (int k = 1; k < nsplit; ++k) sum += red[k * nt + threadIdx.x];
+        const int g = threadIdx.x % ng, q = threadIdx.x / ng;
+        R sum = red[q][g];
+        for (int k = 1; k < nsplit; ++k) sum += red[q][k * ng + g];
         u[t0 + threadIdx.x] = sum;
     }
 }
@@ -353,8 +372,8 @@ int launch_p2p_split(int d, R e2, const rbf_tree *t, const R *xs, const R *lam, 
     switch (d) {
 #define RBF_P2P_CASE(DD)                                                                          \
     case DD:                                                                                      \
-        k_p2p_split<R, DD, KER><<<nleaf, P2P_THREADS, 0, s>>>(e2, t->N, xs, lam, t->leaf_off,      \
-                                                              t->near_off, t->near_idx, u);        \
+        k_p2p_split<R, DD, KER, RBF_P2P_TT><<<nleaf, P2P_THREADS, 0, s>>>(                          \
+            e2, t->N, xs, lam, t->leaf_off, t->near_off, t->near_idx, u);                          \
         break;
         RBF_P2P_CASE(1)
         RBF_P2P_CASE(2)

@@ -93,3 +93,28 @@ def test_clustered_workload_sampled_parity(env):
           f"fp64 rel-L2 {e64[0]:.2e} max {e64[1]:.2e}  fp32 rel-L2 {e32[0]:.2e} max {e32[1]:.2e}")
     assert max(e64) <= 1e-12
     assert max(e32) <= 5e-6
+
+
+def test_fp32_telescoped_coupling_does_not_degrade_with_n(env):
+    """The shared-grid coupling forms every leaf's local expansion as the root
+    expansion, translated, minus the near leaves' terms (telescoped M2L + L2L).
+    In FP32 that difference could lose digits as the root sum grows with N.  At
+    fixed depth (5) and M = 32 the FP32 product is compared element by element with
+    the FP64 product (itself pinned to the oracle at 1e-12) at N = 2^18, 2^20 and
+    2^22 (8 to 128 points per leaf): every element within 5e-6 of max |u|, and the
+    error at 2^22 no more than 4x the error at 2^18 (a cancellation that grew with
+    N would give 16x for a 16x larger root sum)."""
+    rbf, torch = env
+    p = dict(kernel=O.IMQ, eps=2.0, M=32, L=4.0, alpha=4.5)
+    worst = {}
+    for n in (1 << 18, 1 << 20, 1 << 22):
+        X, lam = workloads.uniform(n, 3, 90 + n % 7)
+        t, ld, u64, u32 = _gpu_products(rbf, torch, X, lam, 5, p)
+        e = errs(u32, u64)
+        worst[n] = e[1]
+        print(f"N={n}: fp32 vs fp64 rel-L2 {e[0]:.2e} max {e[1]:.2e} of max |u|")
+        assert max(e) <= 5e-6
+        t.free()
+        del ld
+        torch.cuda.empty_cache()
+    assert worst[1 << 22] <= 4.0 * worst[1 << 18] + 1e-7
