@@ -554,9 +554,11 @@ def batch_measurement(rbf, dev, n_problems=256, steps=5):
     ud = torch.as_tensor(U, device=dev)
     x = torch.zeros_like(ud)
     rep = B.solve(ud, x, restart_m=20, max_iters=10, rtol=1e-12, prec=rbf.FP32)
+    parts = B.time_parts(rbf.FP32, reps=3)
     st = B.stats()
     B.free()
     tree = lay["depth"] > 0
+    dps = st["direct_pairs"] / (parts["direct_ms"] * 1e-3) if parts["direct_ms"] > 0 else None
     return {"problems": n_problems, "systems": int(sum(q["U"].shape[1] for q in probs)),
             "points_x_rhs": int(total), "setup_s": setup,
             "matvec_ms": ms, "value": total / (ms / 1e3), "unit": "points/s (all problems and RHS)",
@@ -565,6 +567,9 @@ def batch_measurement(rbf, dev, n_problems=256, steps=5):
             "choice": {"direct": st["n_direct"], "near_field_only": st["n_near_only"],
                        "fmm": st["n_fmm"]},
             "direct_work_items": st["direct_items"],
+            "parts_ms": parts,
+            "direct_launch": {"pairs": st["direct_pairs"], "pairs_per_s": dps,
+                              "fp32_tflops_at_18_flops_per_pair": dps * 18e-12 if dps else None},
             "graph_kernel_nodes": {"product": st["product_nodes"], "gmres_step": st["step_nodes"]},
             "predicted_ms": st["predicted_ms"], "cost_model_s": st["model"],
             "M_range_tree_problems": ([int(lay["M"][tree].min()), int(lay["M"][tree].max())]

@@ -524,6 +524,7 @@ typedef struct {
     double setup_s;
     double predicted_ms;
     rbf_cost_model model;
+    double direct_pairs;  /* pair evaluations of the direct launch (N^2 per group of 4 columns) */
 } rbf_batch_stats;
 
 /* Choose every problem's product (opts->choice) and build what it needs: a
@@ -542,6 +543,13 @@ RBF_API int rbf_batch_create(const rbf_problem *problems_host, int n_problems, d
 RBF_API int rbf_batch_layout(const rbf_batch *b, int64_t *off_host, int *depth_host, int *M_host,
                              int64_t *total_host);
 RBF_API int rbf_batch_get_stats(const rbf_batch *b, rbf_batch_stats *stats_out);
+/* Device time of the two parts of a batch product, each run alone `reps` times
+ * (after one run outside the timing) with CUDA events on `stream`: the direct
+ * launch and the tree problems' products (enqueued over the batch's streams).
+ * Either part may be empty (0 ms).  Writes the batch's product buffer;
+ * synchronises. */
+RBF_API int rbf_batch_time_parts(rbf_batch *b, rbf_precision prec, int reps, double *direct_ms_host,
+                                 double *trees_ms_host, void *stream);
 /* u = A lambda for every problem and right-hand side (packed device arrays).
  * The first call per precision runs the products once (allocating plans) and
  * captures them into one CUDA graph: the direct sums as one persistent launch

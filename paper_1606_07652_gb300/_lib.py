@@ -72,7 +72,8 @@ class BatchOpts(ctypes.Structure):
 class BatchStats(ctypes.Structure):
     _fields_ = [("n_direct", _c_int), ("n_near_only", _c_int), ("n_fmm", _c_int),
                 ("direct_items", _c_int), ("product_nodes", _c_int), ("step_nodes", _c_int),
-                ("setup_s", _c_dbl), ("predicted_ms", _c_dbl), ("model", CostModel)]
+                ("setup_s", _c_dbl), ("predicted_ms", _c_dbl), ("model", CostModel),
+                ("direct_pairs", _c_dbl)]
 
 
 BATCH_AUTO, BATCH_FMM, BATCH_DIRECT = 0, 1, 2
@@ -157,6 +158,7 @@ def load():
     lib.rbf_batch_create.argtypes = [_c_vp, _c_int, _c_dbl, _c_vp, P(_c_vp)]
     lib.rbf_batch_create_opts.argtypes = [_c_vp, _c_int, P(BatchOpts), _c_vp, P(_c_vp)]
     lib.rbf_batch_get_stats.argtypes = [_c_vp, P(BatchStats)]
+    lib.rbf_batch_time_parts.argtypes = [_c_vp, _c_int, _c_int, P(_c_dbl), P(_c_dbl), _c_vp]
     lib.rbf_cost_calibrate.argtypes = [P(CostModel), _c_vp]
     lib.rbf_autotune_cost.argtypes = [_c_int, _c_dbl, _c_int, _c_i64, _c_int, _c_dbl, _c_dbl,
                                       P(CostModel), P(FmmParams), P(_c_int), P(_c_dbl), P(_c_dbl)]
@@ -741,6 +743,13 @@ class Batch:
         out = {k: getattr(st, k) for k, _ in BatchStats._fields_ if k != "model"}
         out["model"] = st.model.as_dict()
         return out
+
+    def time_parts(self, prec=FP32, reps=3) -> dict:
+        """rbf_batch_time_parts: device ms of the direct launch and of the tree problems."""
+        dm, tm = _c_dbl(0), _c_dbl(0)
+        _check(load().rbf_batch_time_parts(self._h, prec, int(reps), ctypes.byref(dm),
+                                           ctypes.byref(tm), _stream()), "rbf_batch_time_parts")
+        return {"direct_ms": dm.value, "trees_ms": tm.value}
 
     def _packed(self, *named):
         tot = self.layout()["total"]

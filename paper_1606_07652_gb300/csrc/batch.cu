@@ -842,6 +842,7 @@ extern "C" int rbf_batch_create_opts(const rbf_problem *probs, int np, const rbf
         if (D == 0) {
             direct.push_back(p);
             ++b->stats.n_direct;
+            b->stats.direct_pairs += (double)q.N * (double)q.N * ((q.nrhs + 3) / 4);
         } else {
             std::vector<double> lo(q.d, 0.0);
             st = rbf_tree_build(q.X, q.N, q.d, lo.data(), 1.0, D, stream, &t);
@@ -937,6 +938,43 @@ static int batch_enqueue(rbf_batch *b, int prec, cudaStream_t s)
         RBF_CUDA_TRY(cudaEventRecord(b->events[q], b->streams[q]));
         RBF_CUDA_TRY(cudaStreamWaitEvent(s, b->events[q], 0));
     }
+    return RBF_OK;
+}
+
+extern "C" int rbf_batch_time_parts(rbf_batch *b, rbf_precision prec, int reps, double *direct_ms,
+                                    double *trees_ms, void *stream)
+{
+    RBF_REQUIRE(b && direct_ms && trees_ms && reps >= 1, "rbf_batch_time_parts: bad arguments");
+    RBF_REQUIRE(prec == RBF_FP32 || prec == RBF_FP64, "rbf_batch_time_parts: precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    RBF_CUDA_TRY(cudaEventCreate(&e0));
+    RBF_CUDA_TRY(cudaEventCreate(&e1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } ev{e0, e1};
+    // the tree problems alone: the direct set hidden for the duration
+    rbf_direct_set saved = b->direct;
+    b->direct.np = 0;
+    auto trees = [&]() { return batch_enqueue(b, prec, s); };
+    int st = trees();
+    float ms = 0.f;
+    if (st == RBF_OK && cudaEventRecord(e0, s) != cudaSuccess) st = RBF_ECUDA;
+    for (int r = 0; r < reps && st == RBF_OK; ++r) st = trees();
+    if (st == RBF_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = RBF_ECUDA;
+    b->direct = saved;
+    RBF_TRY(st);
+    *trees_ms = b->tree_probs.empty() ? 0.0 : (double)ms / reps;
+    RBF_TRY(rbf_direct_set_run(&b->direct, prec, b->lam, b->u, s));
+    RBF_CUDA_TRY(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) RBF_TRY(rbf_direct_set_run(&b->direct, prec, b->lam, b->u, s));
+    RBF_CUDA_TRY(cudaEventRecord(e1, s));
+    RBF_CUDA_TRY(cudaEventSynchronize(e1));
+    RBF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    *direct_ms = b->direct.np == 0 ? 0.0 : (double)ms / reps;
     return RBF_OK;
 }
 

@@ -80,10 +80,20 @@
 #ifndef RBF_L2P_POINTS
 #define RBF_L2P_POINTS 2
 #endif
-// L2P partial sums: 1 = one shared-memory slot per thread and point, reduced
-// once per chunk; 0 = warp shuffles per point
 // FP32 3-D grouped coupling: modes per thread (1 or 2; two need 141 registers and ran
 // slower, 3.53 against 3.42 ms at the 3-D M = 32 product)
+#ifndef RBF_M2L_MP
+#define RBF_M2L_MP 1
+#endif
+// 3-D coupling by pencils of 2 x 2 x 8 leaves (1) or by parent blocks (0)
+#ifndef RBF_M2L_PENCIL
+#define RBF_M2L_PENCIL 1
+#endif
+#ifndef RBF_M2L_PENCIL_MINB
+#define RBF_M2L_PENCIL_MINB 6          // resident CTAs of the FP32 pencil kernel (80 registers)
+#endif
+// grouped coupling: resident CTAs of 128 threads the register budget targets
+// (8: 64 registers, no spills; 3.43 -> 3.25 ms against the compiler's 71 registers)
 #ifndef RBF_M2L_MINB
 #define RBF_M2L_MINB 8                 // resident CTAs of 128 threads: 64 registers, no spills
 #endif
@@ -92,9 +102,8 @@
 #else
 #define RBF_M2L_BOUNDS __launch_bounds__(128)
 #endif
-#ifndef RBF_M2L_MP
-#define RBF_M2L_MP 1
-#endif
+// L2P partial sums: 1 = one shared-memory slot per thread and point, reduced
+// once per chunk; 0 = warp shuffles per point
 #ifndef RBF_L2P_SMEMRED
 #define RBF_L2P_SMEMRED 1
 #endif
@@ -1381,6 +1390,122 @@ int rbf_run_m2m(rbf_tree *t, const rbf_plan *p, const cplx<R> *VD, cudaStream_t 
     return RBF_OK;
 }
 
+// 3-D coupling by pencils: one CTA per pencil of 2 x 2 x RBF_PENCIL_Z leaves and
+// chunk of 128 modes, one mode per thread.  The thread walks the planes z0 - 1 ..
+// z0 + Z of the pencil's 4 x 4 (x, y) neighbourhood: each plane's 16 values are
+// filtered along x (three taps) and y into the 2 x 2 plane of the pencil, a window
+// of three filtered planes gives the z taps of the plane in the middle, and its four
+// targets L_a = omega C (e^{i xi.(c_a - c_0)} V_0 - S_a) are written.  Every
+// neighbour value is read 16 (Z + 2) / (4 Z) = 5 times per target plane instead of 8
+// times by the parent-block kernel, and a target costs 8 complex MACs instead of 14.
+template <typename R>
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? RBF_M2L_PENCIL_MINB : 3) k_m2l_pencil(int M, int D, int n1, int nmode, int64_t ms,
+                                            const cplx<R> *shD, const R *omegaC,
+                                            const cplx<R> *root_ph, const int4 *seg,
+                                            const int32_t *pnb, const cplx<R> *V0,
+                                            const cplx<R> *VD, const cplx<R> *Vzero, cplx<R> *Lx)
+{
+    using C = cplx<R>;
+    constexpr int Z = RBF_PENCIL_Z, NP = (Z + 2) * 16;
+    __shared__ const C *base[NP];   // expansion of each neighbourhood entry (absent: zeros)
+    __shared__ int32_t nb[NP];
+    const int sgi = blockIdx.x;
+    for (int q = threadIdx.x; q < NP; q += blockDim.x) {
+        const int32_t b = pnb[(int64_t)sgi * NP + q];
+        nb[q] = b;
+        base[q] = b >= 0 ? VD + (int64_t)b * ms : Vzero;
+    }
+    __syncthreads();
+    const int m = blockIdx.y * blockDim.x + threadIdx.x;
+    if (m >= nmode) return;
+    int kidx[3];
+    {
+        int r = m;
+        kidx[2] = r % n1;
+        r /= n1;
+        kidx[1] = r % n1;
+        r /= n1;
+        kidx[0] = r + M / 2;
+    }
+    // Q_t = e^{-i xi_k w_D} = (e^{-i xi_k w_D / 2})^2 from the plan's half-shift table
+    C Q[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const C hq = shD[kidx[t]];
+        Q[t] = cmul(hq, hq);
+    }
+    const int4 sg = seg[sgi];
+    const int64_t nk = (int64_t)1 << D;
+    const int x0 = 2 * sg.x, y0 = 2 * sg.y, z0 = sg.z * Z;
+    // e^{i xi.(c_a - c_0)} V_0 for the pencil's four (x, y) columns; z per plane
+    C RV[4];
+    {
+        const C v0 = V0[m];
+        C px[2], py[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            px[j] = root_ph[((int64_t)0 * nk + x0 + j) * n1 + kidx[0]];
+            py[j] = root_ph[((int64_t)1 * nk + y0 + j) * n1 + kidx[1]];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) RV[c] = cmul(cmul(px[c & 1], py[c >> 1]), v0);
+    }
+    const R w = omegaC[m];
+    // 3-tap sum for targets at block positions 1 and 2 of a line v[0..3]
+    auto tap = [&](const C *v, C q, C *out) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            C s = v[j + 1];
+            cmac(s, cconj(q), v[j]);
+            cmac(s, q, v[j + 2]);
+            out[j] = s;
+        }
+    };
+    C W0[4], W1[4], W2[4];
+#pragma unroll
+    for (int zz = 0; zz < Z + 2; ++zz) {
+        C s1[4][2];  // [y line][x target]
+#pragma unroll
+        for (int i1 = 0; i1 < 4; ++i1) {
+            C v[4];
+#pragma unroll
+            for (int i0 = 0; i0 < 4; ++i0) v[i0] = base[zz * 16 + i1 * 4 + i0][m];
+            tap(v, Q[0], s1[i1]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            W0[c] = W1[c];
+            W1[c] = W2[c];
+        }
+#pragma unroll
+        for (int j0 = 0; j0 < 2; ++j0) {
+            C v[4], o[2];
+#pragma unroll
+            for (int i1 = 0; i1 < 4; ++i1) v[i1] = s1[i1][j0];
+            tap(v, Q[1], o);
+            W2[j0] = o[0];
+            W2[j0 + 2] = o[1];
+        }
+        if (zz >= 2) {
+            const int pl = zz - 1;  // plane of the targets, 1 .. Z
+            const C rz = root_ph[((int64_t)2 * nk + z0 + pl - 1) * n1 + kidx[2]];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int a = nb[pl * 16 + ((c >> 1) + 1) * 4 + (c & 1) + 1];
+                if (a < 0) continue;
+                C S = W1[c];
+                cmac(S, cconj(Q[2]), W0[c]);
+                cmac(S, Q[2], W2[c]);
+                const C r = cmul(RV[c], rz);
+                C out;
+                out.x = w * (r.x - S.x);
+                out.y = w * (r.y - S.y);
+                Lx[(int64_t)a * ms + m] = out;
+            }
+        }
+    }
+}
+
 // coupling of all levels plus the downsweep: leaf local expansions L from the
 // leaf expansions VD and the root expansion V[0] (left by rbf_run_m2m)
 template <typename R>
@@ -1390,7 +1515,13 @@ int rbf_run_m2l(rbf_tree *t, const rbf_plan *p, const cplx<R> *VD, cplx<R> *L, c
     const int d = t->d, D = t->D;
     rbf_pass_timer tm(t, RBF_PASS_M2L, s);
     const C *V0 = (const C *)p->V[0];
-    if (d <= 3) {
+    if (RBF_M2L_PENCIL && d == 3 && t->npz > 0) {
+        k_m2l_pencil<R><<<dim3(t->npz, ceil_div(p->nmode, 128)), 128, 0, s>>>(
+            p->M, D, p->n1, (int)p->nmode, p->mstride, (const C *)p->shift_ph + (int64_t)D * p->n1,
+            (const R *)p->omegaC, (const C *)p->root_ph, t->pz_seg, t->pz_nb, V0, VD,
+            (const C *)p->Vzero, L);
+        RBF_LAUNCH_CHECK();
+    } else if (d <= 3) {
         const int gb = 128;
 #define RBF_M2L_GRP(DD, MP)                                                                        \
     k_m2l_grp<R, DD, MP><<<dim3(t->lev[D - 1].nbox, ceil_div(p->nmode, gb * MP)), gb, 0, s>>>(      \

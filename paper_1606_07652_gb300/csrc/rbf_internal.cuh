@@ -106,9 +106,27 @@ __host__ __device__ inline double rbf_phi64(int kernel, double e2r2)
 // Phi in the product's arithmetic, the kernel fixed at compile time:
 // exp(-(eps r)^2), 1/sqrt(1 + (eps r)^2), sqrt(1 + (eps r)^2) or
 // (1 - eps r)_+^3 (3 eps r + 1).
+#ifndef RBF_PHI_APPROX
+#define RBF_PHI_APPROX 1
+#endif
 template <int KER>
 __device__ __forceinline__ float phi_r2(float e2, float r2)
 {
+#if RBF_PHI_APPROX
+    // the special-function unit's approximations, flushing denormals: the
+    // argument of the reciprocal square root is >= 1 and a denormal exponential
+    // is below 2^-126 of the largest term
+    if (KER == RBF_GAUSSIAN) {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-e2 * r2));
+        return y;
+    }
+    if (KER == RBF_IMQ) {
+        float y;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fmaf(e2, r2, 1.0f)));
+        return y;
+    }
+#endif
     if (KER == RBF_GAUSSIAN) return exp2f(-e2 * r2);  // e2 holds eps^2 * log2(e)
     if (KER == RBF_IMQ) return rsqrtf(fmaf(e2, r2, 1.0f));
     if (KER == RBF_MQ) return sqrtf(fmaf(e2, r2, 1.0f));
@@ -161,6 +179,10 @@ struct rbf_precond_data {
     double eps = 0.0;
 };
 
+#ifndef RBF_PENCIL_Z
+#define RBF_PENCIL_Z 8
+#endif
+
 struct rbf_tree {
     int64_t N = 0;
     int d = 0, D = 0;
@@ -178,6 +200,11 @@ struct rbf_tree {
     int64_t n_near = 0;
     int32_t max_leaf = 0;
     int32_t *nb4 = nullptr;         // [nbox(D-1)][4^d] leaf ids around each parent (d <= 3)
+    // pencils of the 3-D coupling (D >= 3): 2 x 2 x RBF_PENCIL_Z leaves each, the
+    // leaf ids of the 4 x 4 neighbourhood of its planes z0 - 1 .. z0 + RBF_PENCIL_Z
+    int32_t npz = 0;
+    int4 *pz_seg = nullptr;         // [npz] (X, Y, Zs): leaves 2X..2X+1, 2Y..2Y+1, Zs Z ..
+    int32_t *pz_nb = nullptr;       // [npz][(RBF_PENCIL_Z + 2) * 16]
     rbf_level lev[RBF_MAX_DEPTH + 1];
     rbf_plan *plan[2] = {nullptr, nullptr};  // indexed by rbf_precision
     rbf_prof prof;

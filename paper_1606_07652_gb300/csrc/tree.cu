@@ -22,7 +22,7 @@ __device__ __forceinline__ uint64_t morton_encode(const int64_t *k, int d, int l
     return key;
 }
 
-__device__ __forceinline__ void morton_decode(uint64_t key, int d, int l, int64_t *k)
+__host__ __device__ __forceinline__ void morton_decode(uint64_t key, int d, int l, int64_t *k)
 {
     for (int t = 0; t < d; ++t) k[t] = 0;
     for (int b = 0; b < l; ++b)
@@ -383,7 +383,60 @@ __global__ void k_nb4(const uint64_t *pkey, int32_t np, const uint64_t *leaf_key
     nb4[i] = inside ? find_key(leaf_key, nleaf, morton_encode(kl, d, D)) : -1;
 }
 
+// pencil neighbourhoods: entry (seg, plane, pos) is the leaf at x = 2X - 1 + (pos & 3),
+// y = 2Y - 1 + (pos >> 2), z = Zs RBF_PENCIL_Z - 1 + plane, or -1 (empty or outside)
+__global__ void k_pencil_nb(const int4 *seg, int32_t nseg, const uint64_t *leaf_key, int32_t nleaf,
+                            int D, int32_t *nb)
+{
+    constexpr int NP = (RBF_PENCIL_Z + 2) * 16;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nseg * NP) return;
+    const int4 sg = seg[i / NP];
+    const int e = (int)(i % NP), plane = e / 16, pos = e % 16;
+    int64_t k[3] = {2 * (int64_t)sg.x - 1 + (pos & 3), 2 * (int64_t)sg.y - 1 + (pos >> 2),
+                    (int64_t)sg.z * RBF_PENCIL_Z - 1 + plane};
+    const int64_t kmax = ((int64_t)1 << D) - 1;
+    bool inside = true;
+    for (int t = 0; t < 3; ++t) inside = inside && k[t] >= 0 && k[t] <= kmax;
+    nb[i] = inside ? find_key(leaf_key, nleaf, morton_encode(k, 3, D)) : -1;
+}
+
 }  // namespace
+
+// pencils of the 3-D coupling: every (X, Y, Zs) that holds a level-(D-1) box
+static int build_pencils(rbf_tree *t, cudaStream_t s)
+{
+    const int D = t->D;
+    const int32_t np = t->lev[D - 1].nbox;
+    std::vector<uint64_t> pk(np);
+    RBF_CUDA_TRY(cudaMemcpyAsync(pk.data(), t->lev[D - 1].key, np * sizeof(uint64_t),
+                                 cudaMemcpyDeviceToHost, s));
+    RBF_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<uint64_t> code(np);
+    const int zb = RBF_PENCIL_Z / 2;  // parents per pencil along z
+    for (int32_t i = 0; i < np; ++i) {
+        int64_t k[3];
+        morton_decode(pk[i], 3, D - 1, k);
+        code[i] = ((uint64_t)(k[2] / zb) << 42) | ((uint64_t)k[1] << 21) | (uint64_t)k[0];
+    }
+    std::sort(code.begin(), code.end());
+    code.erase(std::unique(code.begin(), code.end()), code.end());
+    std::vector<int4> seg(code.size());
+    const uint64_t m21 = (1ull << 21) - 1;
+    for (size_t i = 0; i < code.size(); ++i)
+        seg[i] = make_int4((int)(code[i] & m21), (int)((code[i] >> 21) & m21), (int)(code[i] >> 42), 0);
+    t->npz = (int32_t)seg.size();
+    const int64_t n = (int64_t)t->npz * (RBF_PENCIL_Z + 2) * 16;
+    RBF_TRY(rbf_alloc(&t->pz_seg, seg.size()));
+    RBF_TRY(rbf_alloc(&t->pz_nb, n));
+    RBF_CUDA_TRY(cudaMemcpyAsync(t->pz_seg, seg.data(), seg.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice, s));
+    k_pencil_nb<<<ceil_div(n, 256), 256, 0, s>>>(t->pz_seg, t->npz, t->lev[D].key, t->nleaf(), D,
+                                                 t->pz_nb);
+    RBF_LAUNCH_CHECK();
+    RBF_CUDA_TRY(cudaStreamSynchronize(s));  // seg goes out of scope
+    return RBF_OK;
+}
 
 // ----------------------------------------------------------- host side ----
 int rbf_scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total_host,
@@ -549,6 +602,7 @@ static int build_impl(rbf_tree *t, const double *X, cudaStream_t s)
                                               t->nb4);
         RBF_LAUNCH_CHECK();
     }
+    if (d == 3 && D >= 3 && ((int64_t)1 << D) % RBF_PENCIL_Z == 0) RBF_TRY(build_pencils(t, s));
     RBF_CUDA_TRY(cudaStreamSynchronize(s));
     rbf_free(cnt);
     return RBF_OK;
@@ -729,6 +783,8 @@ extern "C" void rbf_tree_free(rbf_tree *t)
     rbf_free(t->near_off);
     rbf_free(t->near_idx);
     rbf_free(t->nb4);
+    rbf_free(t->pz_seg);
+    rbf_free(t->pz_nb);
     for (int l = 0; l <= RBF_MAX_DEPTH; ++l) {
         rbf_free(t->lev[l].key);
         rbf_free(t->lev[l].parent);

@@ -217,6 +217,11 @@ def test_auto_batch_mixed_matches_oracle_and_single_products(env):
     assert st["n_near_only"] + st["n_fmm"] >= 1
     lam = rng.standard_normal(lay["total"])
     u = _batch_product(B, torch, lam, rbf.FP32)
+    parts = B.time_parts(rbf.FP32, reps=2)
+    assert parts["direct_ms"] > 0 and parts["trees_ms"] > 0, parts
+    assert B.stats()["direct_pairs"] == sum(float(q["X"].shape[0]) ** 2 for q, D in
+                                            zip(probs, lay["depth"]) if D == 0)
+    u = _batch_product(B, torch, lam, rbf.FP32)   # the timing reused the product buffer
     for p, q in enumerate(probs):
         X = q["X"].cpu().numpy()
         N, nr = X.shape[0], q["nrhs"]
