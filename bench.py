@@ -662,11 +662,11 @@ def solve_leg(rbf, dev, n, depth, fp64_iters, fp32_iters):
 
 def learned_gain_leg(rbf, dev, n1=64, eh=1.2):
     """A regime where local cardinal functions are local: 3-D quasi-uniform centres (a
-    jittered n1^3 grid, spacing h = 1/n1), Gaussian eps = eh / h.  The autotuner picks no
-    far field (the kernel is below 1e-10 beyond one leaf).  Solves to 1e-8 with FP64 and
-    with FP32 inner products: plain, learned P (a 3 x 256 network trained at this eps*h on
-    65,536 of the centres; the time to build P is counted with the solve, the one-off
-    training is reported apart) and exact local cardinal P."""
+    jittered n1^3 grid, spacing h = 1/n1), Gaussian eps = eh / h.  The cost-model autotuner
+    picks no far field (the kernel is below 1e-10 beyond one leaf) and the depth.  Solves to
+    1e-8 with FP64 and with FP32 inner products: plain, learned P (a 3 x 256 network trained
+    at this eps*h on 65,536 of the centres; the time to build P is counted with the solve,
+    the one-off training is reported apart) and exact local cardinal P."""
     import torch
     import workloads
     from paper_1606_07652_gb300 import _lib
@@ -674,7 +674,7 @@ def learned_gain_leg(rbf, dev, n1=64, eh=1.2):
     n = len(X)
     u = np.sin(2 * np.pi * X[:, 0]) * np.cos(2 * np.pi * X[:, 1]) * np.exp(-X[:, 2])
     eps = eh * n1
-    prm = _lib.autotune(rbf.GAUSSIAN, eps, 3, n, 1e-10)
+    prm = _lib.autotune_cost(rbf.GAUSSIAN, eps, 3, n, 1, 1e-10, _lib.cost_calibrate())
     Xd = torch.as_tensor(X, device=dev)
     ud = torch.as_tensor(u, device=dev)
     t = rbf.tree_build(Xd, lo=np.zeros(3), side=1.0, depth=prm["depth"])
@@ -725,6 +725,8 @@ def solve_measurement(rbf, dev, big=True):
     if big:
         out["n1048576"] = solve_leg(rbf, dev, 1 << 20, 7, fp64_iters=60, fp32_iters=600)
     out["learned_gain"] = learned_gain_leg(rbf, dev)
+    if big:   # the same regime at about 10^6 centres (a jittered 102^3 grid)
+        out["learned_gain_1m"] = learned_gain_leg(rbf, dev, n1=102)
     return out
 
 

@@ -276,31 +276,30 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, cons
     for (int s0 = 0; s0 < nsrc; s0 += P2P_SCHUNK) {
         const int cnt = min(P2P_SCHUNK, nsrc - s0);
         __syncthreads();
-        for (int v = threadIdx.x; v < cnt; v += P2P_THREADS) {
-            const int vv = s0 + v;
-            int lo = 0, hi = ne - 1;
-            while (lo < hi) {  // last range with rpre[e] <= vv
-                const int mid = (lo + hi + 1) >> 1;
-                if (rpre[mid] <= vv) lo = mid;
-                else hi = mid - 1;
-            }
-            const int64_t j = rstart[lo] + (vv - rpre[lo]);
-            R c[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
+        // warp w copies the parts of ranges w, w + 4, ... that fall in the chunk,
+        // lane by lane (consecutive lanes read consecutive points)
+        for (int e = threadIdx.x >> 5; e < ne; e += P2P_WARPS) {
+            const int b0 = max(rpre[e], s0), b1 = min(rpre[e + 1], s0 + cnt);
+            for (int vv = b0 + (threadIdx.x & 31); vv < b1; vv += 32) {
+                const int v = vv - s0;
+                const int64_t j = rstart[e] + (vv - rpre[e]);
+                R c[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
 #pragma unroll
-            for (int t = 0; t < DIM; ++t) c[t] = xs[(int64_t)t * N + j];
-            S4 r0;
-            r0.x = c[0];
-            r0.y = c[1];
-            r0.z = c[2];
-            r0.w = lam[j];
-            src[REC * v] = r0;
-            if (REC == 2) {
-                S4 r1;
-                r1.x = c[3];
-                r1.y = c[4];
-                r1.z = c[5];
-                r1.w = (R)0;
-                src[REC * v + 1] = r1;
+                for (int t = 0; t < DIM; ++t) c[t] = xs[(int64_t)t * N + j];
+                S4 r0;
+                r0.x = c[0];
+                r0.y = c[1];
+                r0.z = c[2];
+                r0.w = lam[j];
+                src[REC * v] = r0;
+                if (REC == 2) {
+                    S4 r1;
+                    r1.x = c[3];
+                    r1.y = c[4];
+                    r1.z = c[5];
+                    r1.w = (R)0;
+                    src[REC * v + 1] = r1;
+                }
             }
         }
         __syncthreads();
