@@ -1390,6 +1390,8 @@ int rbf_run_m2m(rbf_tree *t, const rbf_plan *p, const cplx<R> *VD, cudaStream_t 
     return RBF_OK;
 }
 
+namespace {
+
 // 3-D coupling by pencils: one CTA per pencil of 2 x 2 x RBF_PENCIL_Z leaves and
 // chunk of 128 modes, one mode per thread.  The thread walks the planes z0 - 1 ..
 // z0 + Z of the pencil's 4 x 4 (x, y) neighbourhood: each plane's 16 values are
@@ -1505,6 +1507,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? RBF_M2L_PENCIL_MINB : 3)
         }
     }
 }
+
+}  // namespace
 
 // coupling of all levels plus the downsweep: leaf local expansions L from the
 // leaf expansions VD and the root expansion V[0] (left by rbf_run_m2m)
