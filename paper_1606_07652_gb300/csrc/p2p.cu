@@ -22,6 +22,9 @@ constexpr int P2P_STAGE_BYTES = 16384;         // shared memory for staged sourc
 #ifndef RBF_P2P_TGMAX
 #define RBF_P2P_TGMAX 4                        // target groups of 32 per pass, at most
 #endif
+#ifndef RBF_P2P_PRESCALE
+#define RBF_P2P_PRESCALE 1                     // split kernel: Phi from pre-scaled coordinates
+#endif
 #ifndef RBF_P2P_TT
 #define RBF_P2P_TT 2                           // targets per thread of the split kernel
 #endif
@@ -261,12 +264,14 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, cons
     const int nsplit = P2P_THREADS / ng;
     const int grp = threadIdx.x % ng, sp = threadIdx.x / ng;
     const bool active = sp < nsplit;
+    // coordinates scaled by sqrt(e2) (RBF_P2P_PRESCALE): Phi from phi_s
+    const R sc = RBF_P2P_PRESCALE ? sqrt(e2) : (R)1;
     R xt[TT][DIM];
 #pragma unroll
     for (int q = 0; q < TT; ++q) {
         const int tq = min(grp + q * ng, nt - 1);
 #pragma unroll
-        for (int t = 0; t < DIM; ++t) xt[q][t] = xs[(int64_t)t * N + t0 + tq];
+        for (int t = 0; t < DIM; ++t) xt[q][t] = sc * xs[(int64_t)t * N + t0 + tq];
     }
     R acc[TT][SU];
 #pragma unroll
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, cons
                 const int64_t j = rstart[e] + (vv - rpre[e]);
                 R c[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
 #pragma unroll
-                for (int t = 0; t < DIM; ++t) c[t] = xs[(int64_t)t * N + j];
+                for (int t = 0; t < DIM; ++t) c[t] = sc * xs[(int64_t)t * N + j];
                 S4 r0;
                 r0.x = c[0];
                 r0.y = c[1];
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, cons
 #pragma unroll
                 for (int q = 0; q < TT; ++q) {
                     R d0 = xt[q][0] - r0.x;
-                    R r2 = d0 * d0;
+                    R r2 = RBF_P2P_PRESCALE ? fma(d0, d0, (R)phi_c0<KER>()) : d0 * d0;
                     if (DIM > 1) {
                         R d1 = xt[q][DIM > 1 ? 1 : 0] - r0.y;
                         r2 = fma(d1, d1, r2);
@@ -339,7 +344,8 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, cons
                         R d5 = xt[q][DIM > 5 ? 5 : 0] - r1.z;
                         r2 = fma(d5, d5, r2);
                     }
-                    acc[q][k] = fma(wgt, phi_r2<KER>(e2, r2), acc[q][k]);
+                    const R ph = RBF_P2P_PRESCALE ? phi_s<KER>(r2) : phi_r2<KER>(e2, r2);
+                    acc[q][k] = fma(wgt, ph, acc[q][k]);
                 }
             }
         };

@@ -145,6 +145,47 @@ __device__ __forceinline__ double phi_r2(double e2, double r2)
     return t * t * t * fma(3.0, q, 1.0);
 }
 
+// Phi from s = c0 + |e (x_i - x_j)|^2 with coordinates pre-scaled by e = sqrt(e2)
+// and c0 = 1 for the (inverse) multiquadric, 0 otherwise (phi_r2's e2 folded into
+// the coordinates, and its "+ 1" into the sum: one instruction less per pair)
+template <int KER>
+__device__ __forceinline__ constexpr float phi_c0()
+{
+    return KER == RBF_IMQ || KER == RBF_MQ ? 1.0f : 0.0f;
+}
+template <int KER>
+__device__ __forceinline__ float phi_s(float x)
+{
+#if RBF_PHI_APPROX
+    if (KER == RBF_GAUSSIAN) {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x));
+        return y;
+    }
+    if (KER == RBF_IMQ) {
+        float y;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+#endif
+    if (KER == RBF_GAUSSIAN) return exp2f(-x);
+    if (KER == RBF_IMQ) return rsqrtf(x);
+    if (KER == RBF_MQ) return sqrtf(x);
+    const float q = sqrtf(x);
+    const float t = fmaxf(1.0f - q, 0.0f);
+    return t * t * t * fmaf(3.0f, q, 1.0f);
+}
+template <int KER>
+__device__ __forceinline__ double phi_s(double x)
+{
+    if (KER == RBF_GAUSSIAN) return exp(-x);
+    if (KER == RBF_IMQ) return rsqrt(x);
+    if (KER == RBF_MQ) return sqrt(x);
+    const double q = sqrt(x);
+    const double t = fmax(1.0 - q, 0.0);
+    return t * t * t * fma(3.0, q, 1.0);
+}
+
 __device__ __forceinline__ void sincos_r(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_r(double x, double *s, double *c) { sincos(x, s, c); }
 
