@@ -16,6 +16,7 @@
 // the multiquadric sum large terms of both signs).  Padded sources carry lambda = 0
 // and finite coordinates, so every chunk runs the full unrolled loop.
 #include <algorithm>
+#include <cmath>
 #include <numeric>
 
 #include "rbf_internal.cuh"
@@ -70,9 +71,8 @@ __device__ __forceinline__ void direct_item(const DirectArgs &a, const int4 w,
     const V *X = reinterpret_cast<const V *>(a.x) + a.xoff[p];
     const int nc = min(4, a.nrhs[p] - 4 * cg);
     const double *L = a.lam + off + (int64_t)4 * cg * N;
-    R e2 = (R)(a.eps[p] * a.eps[p]);
-    // the FP32 Gaussian goes through exp2, so fold log2(e) into eps^2
-    if (sizeof(R) == 4 && KER == RBF_GAUSSIAN) e2 = (R)(a.eps[p] * a.eps[p] * 1.4426950408889634);
+    // the coordinate records are pre-scaled by sqrt(e2) (k_pack_coords): Phi from phi_s
+    constexpr R c0 = (R)phi_c0<KER>();
     R xt[TT][DIM];
 #pragma unroll
     for (int k = 0; k < TT; ++k) {
@@ -121,7 +121,7 @@ __device__ __forceinline__ void direct_item(const DirectArgs &a, const int4 w,
 #pragma unroll
                 for (int k = 0; k < TT; ++k) {
                     const R dx = xt[k][0] - xs.x;
-                    R r2 = dx * dx;
+                    R r2 = fma(dx, dx, c0);
                     if (DIM > 1) {
                         const R dy = xt[k][DIM > 1 ? 1 : 0] - xs.y;
                         r2 = fma(dy, dy, r2);
@@ -134,7 +134,7 @@ __device__ __forceinline__ void direct_item(const DirectArgs &a, const int4 w,
                         const R dw = xt[k][DIM > 3 ? 3 : 0] - xs.w;
                         r2 = fma(dw, dw, r2);
                     }
-                    const R ph = phi_r2<KER>(e2, r2);
+                    const R ph = phi_s<KER>(r2);
                     c[k][0] = fma(ph, ls.x, c[k][0]);
                     c[k][1] = fma(ph, ls.y, c[k][1]);
                     c[k][2] = fma(ph, ls.z, c[k][2]);
@@ -200,20 +200,23 @@ __global__ void __launch_bounds__(DB_T) k_direct_batch(const DirectArgs a)
     }
 }
 
-// records of 4 coordinates per point (zero-padded) from X [n][d] FP64
-__global__ void k_pack_coords(const double *X, int64_t n, int d, double4_32a *x64, float4 *x32)
+// records of 4 coordinates per point (zero-padded) from X [n][d] FP64, scaled by
+// sqrt(e2) of each precision (FP32 Gaussian: eps^2 log2(e), for exp2; else eps^2)
+__global__ void k_pack_coords(const double *X, int64_t n, int d, double s64, double s32,
+                              double4_32a *x64, float4 *x32)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int t = 0; t < d; ++t) v[t] = X[i * d + t];
     double4_32a r;
-    r.x = v[0];
-    r.y = v[1];
-    r.z = v[2];
-    r.w = v[3];
+    r.x = s64 * v[0];
+    r.y = s64 * v[1];
+    r.z = s64 * v[2];
+    r.w = s64 * v[3];
     x64[i] = r;
-    x32[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+    x32[i] = make_float4((float)(s32 * v[0]), (float)(s32 * v[1]), (float)(s32 * v[2]),
+                         (float)(s32 * v[3]));
 }
 
 template <typename R>
@@ -294,8 +297,10 @@ int rbf_direct_set_build(rbf_direct_set *ds, const rbf_problem *probs, const int
     RBF_CUDA_TRY(cudaMemcpyAsync(ds->eps, eps.data(), ds->np * sizeof(double), cudaMemcpyHostToDevice, s));
     for (int k = 0; k < ds->np; ++k) {
         const rbf_problem &q = probs[which[k]];
+        const double s32 = q.kernel == RBF_GAUSSIAN ? q.eps * std::sqrt(1.4426950408889634) : q.eps;
         k_pack_coords<<<ceil_div(q.N, 256), 256, 0, s>>>(
-            q.X, q.N, q.d, reinterpret_cast<double4_32a *>(ds->x64) + xo[k], ds->x32 + xo[k]);
+            q.X, q.N, q.d, q.eps, s32, reinterpret_cast<double4_32a *>(ds->x64) + xo[k],
+            ds->x32 + xo[k]);
         RBF_LAUNCH_CHECK();
     }
     ds->grid32 = resident_grid<float>(ds->nitems);
