@@ -22,9 +22,6 @@ constexpr int P2P_STAGE_BYTES = 16384;         // shared memory for staged sourc
 #ifndef RBF_P2P_TGMAX
 #define RBF_P2P_TGMAX 4                        // target groups of 32 per pass, at most
 #endif
-#ifndef RBF_P2P_PRESCALE
-#define RBF_P2P_PRESCALE 1                     // split kernel: Phi from pre-scaled coordinates
-#endif
 #ifndef RBF_P2P_TT
 #define RBF_P2P_TT 2                           // targets per thread of the split kernel
 #endif
@@ -117,6 +114,12 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(R e2, int64_t N, const R *x
     near_ranges(e0, ne, near_idx, leaf_off, rstart, rlen, rpre);
     const int nsrc = rpre[ne];
     const int t0 = leaf_off[a], nt = leaf_off[a + 1] - t0;
+    // coordinates relative to the leaf's first point, then scaled: Phi from
+    // phi_s(c0 + sum d^2), rounding relative to the neighbourhood's size
+    const R sc = sqrt(e2);
+    R org[DIM];
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) org[t] = xs[(int64_t)t * N + t0];
     for (int tb = 0; tb < nt; tb += TB) {
         R xt[TG][DIM];
         R acc[TG][SU];
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(R e2, int64_t N, const R *x
 #pragma unroll
             for (int k = 0; k < SU; ++k) acc[g][k] = (R)0;
 #pragma unroll
-            for (int t = 0; t < DIM; ++t) xt[g][t] = i < nt ? xs[(int64_t)t * N + t0 + i] : (R)0;
+            for (int t = 0; t < DIM; ++t) xt[g][t] = i < nt ? sc * (xs[(int64_t)t * N + t0 + i] - org[t]) : (R)0;
         }
         for (int s0 = 0; s0 < nsrc; s0 += P2P_SCHUNK) {
             const int cnt = min(P2P_SCHUNK, nsrc - s0);
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(R e2, int64_t N, const R *x
                 int64_t j = rstart[e] + (vv - rpre[e]);
                 R c[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
 #pragma unroll
-                for (int t = 0; t < DIM; ++t) c[t] = xs[(int64_t)t * N + j];
+                for (int t = 0; t < DIM; ++t) c[t] = sc * (xs[(int64_t)t * N + j] - org[t]);
                 if (REC == 1) {
                     S4 r;
                     r.x = c[0];
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(R e2, int64_t N, const R *x
 #pragma unroll
                     for (int g = 0; g < TG; ++g) {
                         R d0 = xt[g][0] - r0.x;
-                        R r2 = d0 * d0;
+                        R r2 = fma(d0, d0, (R)phi_c0<KER>());
                         if (DIM > 1) {
                             R d1 = xt[g][DIM > 1 ? 1 : 0] - r0.y;
                             r2 = fma(d1, d1, r2);
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(R e2, int64_t N, const R *x
                             R d5 = xt[g][DIM > 5 ? 5 : 0] - r1.z;
                             r2 = fma(d5, d5, r2);
                         }
-                        acc[g][k] = fma(wgt, phi_r2<KER>(e2, r2), acc[g][k]);
+                        acc[g][k] = fma(wgt, phi_s<KER>(r2), acc[g][k]);
                     }
                 }
             }
@@ -264,14 +267,18 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, cons
     const int nsplit = P2P_THREADS / ng;
     const int grp = threadIdx.x % ng, sp = threadIdx.x / ng;
     const bool active = sp < nsplit;
-    // coordinates scaled by sqrt(e2) (RBF_P2P_PRESCALE): Phi from phi_s
-    const R sc = RBF_P2P_PRESCALE ? sqrt(e2) : (R)1;
+    // coordinates relative to the leaf's first point, then scaled: Phi from
+    // phi_s(c0 + sum d^2), rounding relative to the neighbourhood's size
+    const R sc = sqrt(e2);
+    R org[DIM];
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) org[t] = xs[(int64_t)t * N + t0];
     R xt[TT][DIM];
 #pragma unroll
     for (int q = 0; q < TT; ++q) {
         const int tq = min(grp + q * ng, nt - 1);
 #pragma unroll
-        for (int t = 0; t < DIM; ++t) xt[q][t] = sc * xs[(int64_t)t * N + t0 + tq];
+        for (int t = 0; t < DIM; ++t) xt[q][t] = sc * (xs[(int64_t)t * N + t0 + tq] - org[t]);
     }
     R acc[TT][SU];
 #pragma unroll
@@ -290,7 +297,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, cons
                 const int64_t j = rstart[e] + (vv - rpre[e]);
                 R c[8] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
 #pragma unroll
-                for (int t = 0; t < DIM; ++t) c[t] = sc * xs[(int64_t)t * N + j];
+                for (int t = 0; t < DIM; ++t) c[t] = sc * (xs[(int64_t)t * N + j] - org[t]);
                 S4 r0;
                 r0.x = c[0];
                 r0.y = c[1];
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, cons
 #pragma unroll
                 for (int q = 0; q < TT; ++q) {
                     R d0 = xt[q][0] - r0.x;
-                    R r2 = RBF_P2P_PRESCALE ? fma(d0, d0, (R)phi_c0<KER>()) : d0 * d0;
+                    R r2 = fma(d0, d0, (R)phi_c0<KER>());
                     if (DIM > 1) {
                         R d1 = xt[q][DIM > 1 ? 1 : 0] - r0.y;
                         r2 = fma(d1, d1, r2);
@@ -344,7 +351,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_split(R e2, int64_t N, cons
                         R d5 = xt[q][DIM > 5 ? 5 : 0] - r1.z;
                         r2 = fma(d5, d5, r2);
                     }
-                    const R ph = RBF_P2P_PRESCALE ? phi_s<KER>(r2) : phi_r2<KER>(e2, r2);
+                    const R ph = phi_s<KER>(r2);
                     acc[q][k] = fma(wgt, ph, acc[q][k]);
                 }
             }
@@ -475,6 +482,12 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_multi(float e2, int64_t N,
     near_ranges(e0, ne, near_idx, leaf_off, rstart, nullptr, rpre);
     const int nsrc = rpre[ne];
     const int t0 = leaf_off[a], nt = leaf_off[a + 1] - t0;
+    // coordinates relative to the leaf's first point, then scaled: Phi from
+    // phi_s(c0 + sum d^2), rounding relative to the neighbourhood's size
+    const float sc = sqrtf(e2);
+    float org[DIM];
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) org[t] = xs[(int64_t)t * N + t0];
     for (int tb = 0; tb < nt; tb += TB) {
         float xt[TG][DIM];
         float acc[TG][RG];
@@ -482,7 +495,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_multi(float e2, int64_t N,
         for (int g = 0; g < TG; ++g) {
             const int i = tb + g * 32 + lane;
 #pragma unroll
-            for (int t = 0; t < DIM; ++t) xt[g][t] = i < nt ? xs[(int64_t)t * N + t0 + i] : 0.0f;
+            for (int t = 0; t < DIM; ++t) xt[g][t] = i < nt ? sc * (xs[(int64_t)t * N + t0 + i] - org[t]) : 0.0f;
 #pragma unroll
             for (int r = 0; r < RG; ++r) acc[g][r] = 0.0f;
         }
@@ -501,7 +514,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_multi(float e2, int64_t N,
                 const int64_t j = rstart[lo] + (vv - rpre[lo]);
                 float *rec = buf + v * REC;
 #pragma unroll
-                for (int t = 0; t < C4; ++t) rec[t] = t < DIM ? xs[(int64_t)t * N + j] : 0.0f;
+                for (int t = 0; t < C4; ++t) rec[t] = t < DIM ? sc * (xs[(int64_t)t * N + j] - org[t]) : 0.0f;
 #pragma unroll
                 for (int r = 0; r < RG; ++r) rec[C4 + r] = r < G ? lam[(int64_t)r * N + j] : 0.0f;
             }
@@ -528,13 +541,13 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_multi(float e2, int64_t N,
 #pragma unroll
                 for (int g = 0; g < TG; ++g) {
                     if (g < ngrp) {
-                        float r2 = 0.0f;
+                        float r2 = phi_c0<KER>();
 #pragma unroll
                         for (int t = 0; t < DIM; ++t) {
                             const float df = xt[g][t] - xs_[t];
                             r2 = fmaf(df, df, r2);
                         }
-                        const float ph = phi_r2<KER>(e2, r2);
+                        const float ph = phi_s<KER>(r2);
 #pragma unroll
                         for (int r = 0; r < RG; ++r) acc[g][r] = fmaf(l[r], ph, acc[g][r]);
                     }

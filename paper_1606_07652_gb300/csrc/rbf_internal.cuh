@@ -103,51 +103,18 @@ __host__ __device__ inline double rbf_phi64(int kernel, double e2r2)
     return 1.0 / sqrt(1.0 + e2r2);
 }
 
-// Phi in the product's arithmetic, the kernel fixed at compile time:
-// exp(-(eps r)^2), 1/sqrt(1 + (eps r)^2), sqrt(1 + (eps r)^2) or
-// (1 - eps r)_+^3 (3 eps r + 1).
+// FP32 Phi through the special-function unit's approximations (ex2, rsqrt) with
+// denormals flushed: the reciprocal square root's argument is >= 1 and a flushed
+// exponential is below 2^-126 of the largest term
 #ifndef RBF_PHI_APPROX
 #define RBF_PHI_APPROX 1
 #endif
-template <int KER>
-__device__ __forceinline__ float phi_r2(float e2, float r2)
-{
-#if RBF_PHI_APPROX
-    // the special-function unit's approximations, flushing denormals: the
-    // argument of the reciprocal square root is >= 1 and a denormal exponential
-    // is below 2^-126 of the largest term
-    if (KER == RBF_GAUSSIAN) {
-        float y;
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-e2 * r2));
-        return y;
-    }
-    if (KER == RBF_IMQ) {
-        float y;
-        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fmaf(e2, r2, 1.0f)));
-        return y;
-    }
-#endif
-    if (KER == RBF_GAUSSIAN) return exp2f(-e2 * r2);  // e2 holds eps^2 * log2(e)
-    if (KER == RBF_IMQ) return rsqrtf(fmaf(e2, r2, 1.0f));
-    if (KER == RBF_MQ) return sqrtf(fmaf(e2, r2, 1.0f));
-    const float q = sqrtf(e2 * r2);
-    const float t = fmaxf(1.0f - q, 0.0f);
-    return t * t * t * fmaf(3.0f, q, 1.0f);
-}
-template <int KER>
-__device__ __forceinline__ double phi_r2(double e2, double r2)
-{
-    if (KER == RBF_GAUSSIAN) return exp(-e2 * r2);
-    if (KER == RBF_IMQ) return rsqrt(fma(e2, r2, 1.0));
-    if (KER == RBF_MQ) return sqrt(fma(e2, r2, 1.0));
-    const double q = sqrt(e2 * r2);
-    const double t = fmax(1.0 - q, 0.0);
-    return t * t * t * fma(3.0, q, 1.0);
-}
-
-// Phi from s = c0 + |e (x_i - x_j)|^2 with coordinates pre-scaled by e = sqrt(e2)
-// and c0 = 1 for the (inverse) multiquadric, 0 otherwise (phi_r2's e2 folded into
-// the coordinates, and its "+ 1" into the sum: one instruction less per pair)
+// Phi in the product's arithmetic, the kernel fixed at compile time, from
+// s = c0 + |e (x_i - x_j)|^2 with the coordinates pre-scaled by e (e = eps, or
+// eps sqrt(log2 e) for the FP32 Gaussian, which goes through exp2) and c0 = 1 for
+// the multiquadric and its inverse, 0 otherwise: exp(-s), 1/sqrt(s), sqrt(s) or
+// (1 - q)_+^3 (3 q + 1) with q = sqrt(s).  Folding eps^2 into the coordinates and
+// the "1 +" into the sum saves an instruction per pair.
 template <int KER>
 __device__ __forceinline__ constexpr float phi_c0()
 {
