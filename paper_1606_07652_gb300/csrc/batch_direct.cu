@@ -200,15 +200,17 @@ __global__ void __launch_bounds__(DB_T) k_direct_batch(const DirectArgs a)
     }
 }
 
-// records of 4 coordinates per point (zero-padded) from X [n][d] FP64, scaled by
-// sqrt(e2) of each precision (FP32 Gaussian: eps^2 log2(e), for exp2; else eps^2)
+// records of 4 coordinates per point (zero-padded) from X [n][d] FP64, relative to
+// the centre of the root cube [0,1]^d (so that the rounding is relative to half the
+// cube) and scaled by sqrt(e2) of each precision (FP32 Gaussian: eps^2 log2(e), for
+// exp2; else eps^2)
 __global__ void k_pack_coords(const double *X, int64_t n, int d, double s64, double s32,
                               double4_32a *x64, float4 *x32)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int t = 0; t < d; ++t) v[t] = X[i * d + t];
+    for (int t = 0; t < d; ++t) v[t] = X[i * d + t] - 0.5;
     double4_32a r;
     r.x = s64 * v[0];
     r.y = s64 * v[1];

@@ -134,7 +134,7 @@ def test_batch_solve_residuals(env):
 
 def _direct_problems(torch, seed):
     """d = 1..4, all four kernels, 1..6 right-hand sides (two column groups), sizes
-    from one tile to several with ragged tails."""
+    from one tile to several with ragged tails, and two narrow kernels."""
     rng = np.random.default_rng(seed)
     probs = []
     for k, (N, d, kern, nrhs) in enumerate([(1, 2, O.GAUSSIAN, 1), (37, 1, O.IMQ, 2),
@@ -144,6 +144,10 @@ def _direct_problems(torch, seed):
         eps = 0.5 if kern == O.WENDLAND else float(rng.uniform(1, 5))
         probs.append(dict(X=torch.as_tensor(rng.random((N, d)), device="cuda"), kernel=kern,
                           eps=eps, nrhs=nrhs))
+    # narrow kernels: Phi is most sensitive to the rounding of the scaled coordinates
+    for N, d, kern, eps in [(2500, 2, O.GAUSSIAN, 60.0), (1500, 3, O.IMQ, 40.0)]:
+        probs.append(dict(X=torch.as_tensor(rng.random((N, d)), device="cuda"), kernel=kern,
+                          eps=eps, nrhs=2))
     return probs
 
 
