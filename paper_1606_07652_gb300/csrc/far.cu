@@ -15,8 +15,13 @@
 // the weight 2 of the k0 > 0 half is inside omegaC.  P2M and L2P are dense
 // per-leaf contractions  V[row][col] = sum_j A_j[row] B_j[col]  with
 // A_j[row] = lambda_j prod_{t<d-1} E_t[j][k_t] and B_j[col] = E_{d-1}[j][col],
-// E_t[j][k] = e^{-+ i xi_k (x_{j,t} - c_t)}: each thread owns one row and keeps
-// its NC columns in registers, the per-point phase tables sit in shared memory.
+// E_t[j][k] = e^{-+ i xi_k (x_{j,t} - c_t)}, the per-point phase tables in shared
+// memory.  P2M: a thread accumulates one row times a segment of columns.  FP32 L2P
+// (k_l2p_horner2): a warp pair shares 32 rows, each thread holds half a row of the
+// local expansion in registers and sums its columns by Horner's rule in
+// z = e^{i dxi (x_{j,d-1} - c_{d-1})}, in groups of 8 columns shifted by the
+// group's start phase.  3-D M2L (k_m2l_pencil): pencils of 2 x 2 x 8 leaves, the
+// three-tap stencil one dimension at a time with a window of three planes.
 #include <algorithm>
 #include <type_traits>
 
