@@ -277,6 +277,10 @@ def run_ours(args):
                 ach = amount / (ms / 1e3)
                 passes[name].update({"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                                      "frac": ach / peak})
+        if "p2m" in passes:
+            from paper_1606_07652_gb300 import _lib
+            passes["p2m"]["launch_shape"] = {0: "by rule", 1: "dense (measured)",
+                                             2: "wide (measured)"}[_lib.p2m_launch_shape(tree)]
         if "p2p" in passes:
             # one rsqrt per pair (IMQ) on the multi-function unit beside ~11 FP32 flops:
             # the pass is bound by whichever unit its work fills first

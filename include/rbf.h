@@ -288,6 +288,12 @@ RBF_API int rbf_interp_solve(rbf_tree *t, rbf_kernel kernel, double eps, const r
 #define RBF_PASS_PERM 5
 #define RBF_PASS_COUNT 6
 RBF_API int rbf_profile(rbf_tree *t, int enable);
+/* Launch shape of the FP32 P2M that the tree's FP32 plan measured when it was
+ * created (both shapes run twice on the tree, the faster kept; the shapes give
+ * the same bits): *shape_host = 1 dense (five CTAs of up to 192 threads per SM),
+ * 2 wide (four of up to 256), 0 chosen by rule (no FP32 plan yet, fewer than
+ * 16,384 points, column segments wider than 36, nested grids or no far field). */
+RBF_API int rbf_p2m_launch_shape(const rbf_tree *t, int *shape_host);
 RBF_API int rbf_profile_read(rbf_tree *t, double *ms_host, int64_t *launches_host);
 
 /* Measured peak rate of one arithmetic unit of the current device (the

@@ -169,6 +169,7 @@ def load():
     lib.rbf_batch_free.argtypes = [_c_vp]
     lib.rbf_batch_free.restype = None
     lib.rbf_profile.argtypes = [_c_vp, _c_int]
+    lib.rbf_p2m_launch_shape.argtypes = [_c_vp, P(_c_int)]
     lib.rbf_profile_read.argtypes = [_c_vp, _c_vp, _c_vp]
     lib.rbf_tree_free.argtypes = [_c_vp]
     lib.rbf_tree_free.restype = None
@@ -427,6 +428,13 @@ def fmm_matvec_host(tree: Tree, kernel: int, eps: float, lam_host, u_host=None, 
 def profile(tree: Tree, enable: bool = True):
     """rbf_profile: start (and clear) or stop per-pass event timing."""
     _check(load().rbf_profile(tree.handle, int(bool(enable))), "rbf_profile")
+
+
+def p2m_launch_shape(tree: Tree) -> int:
+    """rbf_p2m_launch_shape: 1 dense, 2 wide (measured), 0 by rule."""
+    v = _c_int(0)
+    _check(load().rbf_p2m_launch_shape(tree.handle, ctypes.byref(v)), "rbf_p2m_launch_shape")
+    return v.value
 
 
 PASS_NAMES = ("p2p", "p2m", "m2m", "m2l", "l2p", "perm")

@@ -112,6 +112,14 @@ static void prof_clear(rbf_tree *t)
 
 void rbf_prof_release(rbf_tree *t) { prof_clear(t); }
 
+extern "C" int rbf_p2m_launch_shape(const rbf_tree *t, int *shape_host)
+{
+    RBF_REQUIRE(t && shape_host, "rbf_p2m_launch_shape: NULL argument");
+    const rbf_plan *p = t->plan[RBF_FP32];
+    *shape_host = p ? p->p2m_shape : 0;
+    return RBF_OK;
+}
+
 extern "C" int rbf_profile(rbf_tree *t, int enable)
 {
     RBF_REQUIRE(t != nullptr, "rbf_profile: tree is NULL");

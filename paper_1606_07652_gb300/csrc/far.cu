@@ -151,6 +151,7 @@ struct FarArgs {
     R *u;                  // [N] (L2P out)
     int pch;               // points per shared-memory chunk
     int seg0, seg;         // table segment lengths (even; seg >= columns read per point)
+    int shape;             // P2M launch shape: 0 by rule, 1 dense, 2 wide (measured per plan)
 };
 
 __device__ __forceinline__ void decode_key(uint64_t key, int d, int l, int *k)
@@ -1312,7 +1313,9 @@ int launch_p2m_l2p(bool l2p, const FarArgs<R> &a0, int nleaf, cudaStream_t s)
     // dense shape for leaves of up to 96 points on average and column segments of
     // at most 36 (wider ones spill under its register bound); L2P's short chunks
     // only for leaves of up to 32 points
-    const bool dense = sizeof(R) == 4 && a.N <= 96 * (int64_t)nleaf && NCE <= RBF_L2P_NARROW;
+    bool dense = sizeof(R) == 4 && a.N <= 96 * (int64_t)nleaf && NCE <= RBF_L2P_NARROW;
+    // P2M: the shape measured at plan creation, when there was a choice
+    if (!l2p && a.shape != 0) dense = sizeof(R) == 4 && NCE <= RBF_L2P_NARROW && a.shape == 1;
     const bool small = a.N <= 32 * (int64_t)nleaf;
     const int want = l2p ? (dense && small ? RBF_L2P_PCH_DENSE : RBF_L2P_PCH_WIDE)
                          : (dense ? RBF_P2M_PCH_DENSE : RBF_P2M_PCH_WIDE);
@@ -1609,6 +1612,7 @@ FarArgs<R> far_args(const rbf_tree *t, const rbf_plan *p)
     a.Lx = nullptr;
     a.u = nullptr;
     a.pch = 0;   // set per launch: as many points as fit in ~64 KB of tables, at most 64
+    a.shape = p->p2m_shape;
     a.seg0 = a.seg = 0;
     return a;
 }
@@ -1623,6 +1627,51 @@ int rbf_run_p2m(rbf_tree *t, const rbf_plan *p, const R *lam_s, cplx<R> *V, cuda
     a.V = V;
     rbf_pass_timer tm(t, RBF_PASS_P2M, s);
     return dispatch_p2m_l2p<R>(false, a, t->nleaf(), s);
+}
+
+// P2M launch shape of an FP32 plan, by measurement: both shapes (dense: five
+// CTAs of up to 192 threads; wide: four of up to 256) run P2M twice on the plan's
+// tree, the second run of each timed with CUDA events; the faster one is kept in
+// the plan.  Both shapes accumulate every output over the points in the same
+// order, so the choice changes no bit of the result.  Only where both shapes are
+// built (column segments of at most 36) and the tree is large enough to time.
+int rbf_tune_p2m_shape(rbf_tree *t, rbf_plan *p, cudaStream_t s)
+{
+    p->p2m_shape = 0;
+    if (p->prec != RBF_FP32 || p->M == 0 || t->D < 2 || t->d < 2 || t->N < 16384 ||
+        even_up(p->ncol) > RBF_L2P_NARROW || p->grid != RBF_GRID_SHARED)
+        return RBF_OK;
+    float *lam = nullptr;
+    RBF_TRY(rbf_alloc(&lam, (size_t)t->N));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = RBF_OK;
+    if (cudaMemsetAsync(lam, 0, (size_t)t->N * sizeof(float), s) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        st = RBF_ECUDA;
+    float best = INFINITY;
+    int pick = 0;
+    for (int shape = 1; shape <= 2 && st == RBF_OK; ++shape) {
+        FarArgs<float> a = far_args<float>(t, p);
+        a.lam = lam;
+        a.V = (float2 *)p->V[t->D];
+        a.shape = shape;
+        float ms = 0.f;
+        st = dispatch_p2m_l2p<float>(false, a, t->nleaf(), s);
+        if (st == RBF_OK && cudaEventRecord(e0, s) != cudaSuccess) st = RBF_ECUDA;
+        if (st == RBF_OK) st = dispatch_p2m_l2p<float>(false, a, t->nleaf(), s);
+        if (st == RBF_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            st = RBF_ECUDA;
+        if (st == RBF_OK && ms < best) {
+            best = ms;
+            pick = shape;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    rbf_free(lam);
+    if (st == RBF_OK) p->p2m_shape = pick;
+    return st;
 }
 
 namespace {

@@ -370,6 +370,7 @@ int rbf_plan_get(rbf_tree *t, rbf_kernel kernel, double eps, const rbf_fmm_param
     int st = M == 0 ? RBF_OK
                     : (prec == RBF_FP64 ? build_tables<double>(t, p, s) : build_tables<float>(t, p, s));
     if (st == RBF_OK && fresh) st = prec == RBF_FP64 ? alloc_work<double>(t, p) : alloc_work<float>(t, p);
+    if (st == RBF_OK && fresh && prec == RBF_FP32) st = rbf_tune_p2m_shape(t, p, s);
     if (st == RBF_OK && p->grid == RBF_GRID_NESTED) st = rbf_nested_build(t, p, s);
     if (st != RBF_OK) {
         rbf_plan_free(p);

@@ -282,6 +282,7 @@ struct rbf_plan {
     // nested (scale-invariant) grids of Sec. 4.1.1 (grid == RBF_GRID_NESTED), nested.cu
     int grid = RBF_GRID_SHARED;
     int lagK = 0, lagKT = 0;   // taps of the interpolation and of its transpose
+    int p2m_shape = 0;         // FP32 P2M launch shape measured at creation (0: by rule)
     void *nest_wc[RBF_MAX_DEPTH + 1] = {nullptr};  // [nmode] omega_l C_l, levels 2..D
     void *nest_xi = nullptr;   // [n1] nodes of the leaf grid
     void *nest_ph = nullptr;   // [15][n1] complex translation phases (level independent)
@@ -333,6 +334,7 @@ int rbf_run_far_multi(rbf_tree *t, rbf_plan *p, const float *lam_s, int G, float
                       float *u_far, cudaStream_t s);
 // nonzero when the plan's columns per mode row fit a tensor-core tile
 int rbf_far_multi_supported(const rbf_plan *p);
+int rbf_tune_p2m_shape(rbf_tree *t, rbf_plan *p, cudaStream_t s);
 // nonzero when a bounded device-side wait of a tensor-core kernel gave up
 int rbf_tc_fetch_status(int *flags_host);
 

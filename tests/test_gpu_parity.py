@@ -257,3 +257,35 @@ def test_autotune_picks_no_far_field_for_narrow_kernels(rbf):
     assert narrow["M"] == 0 and narrow["err"] <= 1e-10, narrow
     wide = _lib.autotune(O.GAUSSIAN, 3.0, 3, 1 << 18, 1e-8)
     assert wide["M"] >= 8, wide
+
+
+def test_p2m_launch_shape_is_measured_and_bit_neutral(rbf):
+    """An FP32 plan of a large enough tree times both P2M launch shapes when it is
+    created and keeps the faster (rbf_p2m_launch_shape); a small tree keeps the rule.
+    The shapes accumulate every output over the points in the same order, so two trees
+    of the same points give the same bits whichever shape each picked, and the product
+    matches the oracle's FMM."""
+    import torch
+    from paper_1606_07652_gb300 import _lib
+    X, lam = workloads.uniform(20000, 3, 61)
+    kw = dict(M=24, period_L=4.0, window_alpha=4.5)
+    outs, shapes = [], []
+    for _ in range(2):
+        t = rbf.tree_build(_dev(X), lo=np.zeros(3), side=1.0, depth=3)
+        u = torch.empty(len(X), dtype=torch.float64, device="cuda")
+        rbf.fmm_matvec(t, O.IMQ, 2.0, _dev(lam), u, prec=rbf.FP32, **kw)
+        torch.cuda.synchronize()
+        shapes.append(_lib.p2m_launch_shape(t))
+        outs.append(u.cpu().numpy())
+        t.free()
+    assert all(s in (1, 2) for s in shapes), shapes
+    assert np.array_equal(outs[0], outs[1])
+    T = O.tree(X, np.zeros(3), 1.0, 3)
+    wc = O.coeffs_sampled(O.IMQ, 2.0, 3, 24, 4.0, 4.5, 1.0)
+    assert rel(outs[0], O.fmm(T, lam, O.IMQ, 2.0, wc, 24, 4.0)) <= FP32_TOL
+    Xs, lams = workloads.uniform(5000, 3, 62)
+    ts = rbf.tree_build(_dev(Xs), lo=np.zeros(3), side=1.0, depth=3)
+    us = torch.empty(len(Xs), dtype=torch.float64, device="cuda")
+    rbf.fmm_matvec(ts, O.IMQ, 2.0, _dev(lams), us, prec=rbf.FP32, **kw)
+    assert _lib.p2m_launch_shape(ts) == 0
+    ts.free()
