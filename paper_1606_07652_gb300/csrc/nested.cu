@@ -212,20 +212,29 @@ __global__ void __launch_bounds__(kThreads) k_l2l_first(int M, int n1, int64_t n
     }
     const C *P = Lp + (int64_t)parent[c] * ms;
     const int row0 = (kPhL2L + (bits & 1u)) * n1;
-    C acc{(R)0, (R)0};
+    // taps with k0 >= 0 and k0 < 0 are summed apart, so that the translation of
+    // dimensions 1..d-1 (fr, or fm for the mirrored rest) multiplies each sum once:
+    // sum_a wt ph v fr + conj(sum_a wt ph v fm) = fr S+ + conj(fm S-)  (wt real)
+    C sp{(R)0, (R)0}, sm{(R)0, (R)0};
     for (int a = 0; a < KT; ++a) {
         const int k = tidx[jp * KT + a] - M / 2;
-        const R wt = tw[jp * KT + a];
         const int ka = k >= 0 ? k : -k;
-        const R unw = ka > 0 ? (R)0.5 : (R)1;  // weighted -> plain value at |k0|
-        C v = P[(int64_t)ka * rows + (k >= 0 ? rest : mrest)];
-        v.x *= unw;
-        v.y *= unw;
-        C sv = cmul(cmul(ph[row0 + ka + M / 2], k >= 0 ? fr : fm), v);
-        if (k < 0) sv = cconj(sv);
-        acc.x = fma(wt, sv.x, acc.x);
-        acc.y = fma(wt, sv.y, acc.y);
+        // weighted -> plain value at |k0|: halve the weight of k0 != 0
+        const R wt = ka > 0 ? (R)0.5 * tw[jp * KT + a] : tw[jp * KT + a];
+        const C v = P[(int64_t)ka * rows + (k >= 0 ? rest : mrest)];
+        const C pv = cmul(ph[row0 + ka + M / 2], v);
+        if (k >= 0) {
+            sp.x = fma(wt, pv.x, sp.x);
+            sp.y = fma(wt, pv.y, sp.y);
+        } else {
+            sm.x = fma(wt, pv.x, sm.x);
+            sm.y = fma(wt, pv.y, sm.y);
+        }
     }
+    C acc = cmul(fr, sp);
+    const C tm = cconj(cmul(fm, sm));
+    acc.x += tm.x;
+    acc.y += tm.y;
     const R wgt = jp > M / 2 ? (R)2 : (R)1;  // plain -> weighted at the child's k0
     acc.x *= wgt;
     acc.y *= wgt;
