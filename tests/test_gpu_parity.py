@@ -7,6 +7,8 @@ kernel error at these expansion sizes).  Each bound applies both to the
 relative L2 error and to every element's error relative to max |u_ref|
 (tests/_parity.py).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -263,8 +265,8 @@ def test_p2m_launch_shape_is_measured_and_bit_neutral(rbf):
     """An FP32 plan of a large enough tree times both P2M launch shapes when it is
     created and keeps the faster (rbf_p2m_launch_shape); a small tree keeps the rule.
     The shapes accumulate every output over the points in the same order, so two trees
-    of the same points give the same bits whichever shape each picked, and the product
-    matches the oracle's FMM."""
+    of the same points give the same bits whichever shape each picked (also with each
+    shape forced through RBF_P2M_SHAPE), and the product matches the oracle's FMM."""
     import torch
     from paper_1606_07652_gb300 import _lib
     X, lam = workloads.uniform(20000, 3, 61)
@@ -280,6 +282,26 @@ def test_p2m_launch_shape_is_measured_and_bit_neutral(rbf):
         t.free()
     assert all(s in (1, 2) for s in shapes), shapes
     assert np.array_equal(outs[0], outs[1])
+    # each shape forced in turn (dense, wide): the same bits
+    forced = []
+    old_env = os.environ.get("RBF_P2M_SHAPE")
+    try:
+        for shape in (1, 2):
+            os.environ["RBF_P2M_SHAPE"] = str(shape)
+            t = rbf.tree_build(_dev(X), lo=np.zeros(3), side=1.0, depth=3)
+            u = torch.empty(len(X), dtype=torch.float64, device="cuda")
+            rbf.fmm_matvec(t, O.IMQ, 2.0, _dev(lam), u, prec=rbf.FP32, **kw)
+            torch.cuda.synchronize()
+            assert _lib.p2m_launch_shape(t) == shape
+            forced.append(u.cpu().numpy())
+            t.free()
+    finally:
+        if old_env is None:
+            os.environ.pop("RBF_P2M_SHAPE", None)
+        else:
+            os.environ["RBF_P2M_SHAPE"] = old_env
+    for f in forced:
+        assert np.array_equal(f, outs[0])
     T = O.tree(X, np.zeros(3), 1.0, 3)
     wc = O.coeffs_sampled(O.IMQ, 2.0, 3, 24, 4.0, 4.5, 1.0)
     assert rel(outs[0], O.fmm(T, lam, O.IMQ, 2.0, wc, 24, 4.0)) <= FP32_TOL
